@@ -1,0 +1,352 @@
+"""FP64 CPU oracle for one CPRA training step (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The product path (the CUDA library and
+its Python binding) never calls it and shares no code with it.
+
+What it computes, in the paper's order and notation (Ichikawa & Iwashita,
+"Continuous Parallel Relaxation for Finding Diverse Solutions in
+Combinatorial Optimization Problems"):
+
+  forward   Eq. GCN (App. B.1) twice, with the two-layer architecture of
+            App. C.1: node embeddings h^0 (N x H0) -> conv -> ReLU -> conv
+            (width S) -> sigmoid  =>  P in [0,1]^{N x S}.
+  loss      Eq. (CPRA-loss-function-GNN-penalty) / (...-variation):
+            R = sum_s l(P_:s; C, lambda_s) + gamma * S(P) + nu * Psi(P),
+            S(P) = sum_{i,s} 1 - (2 P_is - 1)^alpha,
+            Psi(P) = -S * sum_i STD_s[P_is]  (population STD, Notation sec.).
+            l is the MIS or MaxCut QUBO of Table "objective-functions"
+            (App. C.3) with x relaxed to P (Background, continuous relaxation).
+  gradient  analytic chain rule through sigmoid, both GCN layers and the
+            node embeddings (plain calculus; no autograd).
+  update    Adam / AdamW (Implementation paragraph of the Experiments section).
+  rounding  x_is = 1[P_is > 0.5] (App. C.2), integer MIS size / violations /
+            MaxCut cut per shot, and the pairwise Hamming sum of Prop. 3.2.
+
+Readings of points the paper leaves open:
+  * annealing sign: S(P) = sum(1 - (2P-1)^alpha) with gamma increasing from
+    negative (convex, P -> 1/2) to positive (binarising), per Theorem 3.1;
+  * d/dp (1-(2p-1)^alpha) = -2 alpha (2p-1)^(alpha-1) (App. A prints the
+    alpha = 2 case only);
+  * every undirected edge counted once in the MIS penalty and the MaxCut sum;
+  * Psi gradient is zero on rows whose variance across shots is exactly 0;
+  * the optional "VAR" diversity form Psi_var = -S^2 sum_i VAR_s[P_is] is the
+    left-hand side of Prop. 3.2 (negated);
+  * parameters: one self weight B^k, one neighbour weight W^k and one bias
+    per layer (this reproduces the parameter counts printed in the tables of
+    the Experiments section); the flat layout is
+    [Wcat1 = [B1|W1] (H1 x 2H0), b1, Wcat2 = [B2|W2] (S x 2H1), b2];
+  * node embeddings are trainable (h^0_{v,theta}, App. C.1) but are not
+    counted as parameters by those tables.
+
+Parity status: every function below is pinned by tests under tests/
+(brute force, closed forms, invariants, finite differences, library
+routines).  Multi-step trajectories are not pinned (the iteration is
+chaotic); parity is per step from identical inputs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MIS = 0
+MAXCUT = 1
+DIV_STD = 0
+DIV_VAR = 1
+
+
+# --------------------------------------------------------------------------
+# graph helpers
+# --------------------------------------------------------------------------
+class Graph:
+    """Symmetric CSR plus the undirected edge list (i < j), in float64."""
+
+    def __init__(self, rowptr, col, weights=None):
+        self.rowptr = np.asarray(rowptr, dtype=np.int64)
+        self.col = np.asarray(col, dtype=np.int64)
+        self.N = len(self.rowptr) - 1
+        self.deg = np.diff(self.rowptr).astype(np.int64)
+        rows = np.repeat(np.arange(self.N, dtype=np.int64), self.deg)
+        self.rows = rows                       # source row of each CSR entry
+        w = np.ones(len(self.col)) if weights is None else np.asarray(weights, np.float64)
+        self.w_csr = w
+        keep = rows < self.col
+        self.ei = rows[keep]                   # undirected edges, each once
+        self.ej = self.col[keep]
+        self.ew = w[keep]
+        # weighted degree sum_j A_ij (MaxCut linear term)
+        self.wdeg = np.zeros(self.N)
+        np.add.at(self.wdeg, rows, w)
+
+
+def mean_aggregate(g: Graph, X: np.ndarray) -> np.ndarray:
+    """a_v = (1/|N(v)|) sum_{u in N(v)} X_u  (Eq. GCN, App. B.1); 0 if isolated."""
+    out = np.zeros((g.N, X.shape[1]))
+    np.add.at(out, g.rows, X[g.col])
+    nz = g.deg > 0
+    out[nz] /= g.deg[nz, None]
+    return out
+
+
+def mean_aggregate_adjoint(g: Graph, Y: np.ndarray) -> np.ndarray:
+    """Adjoint of mean_aggregate: out_u = sum_{v : u in N(v)} Y_v / |N(v)|.
+
+    Written as the literal transpose: every CSR entry (v -> u) of row v sends
+    Y_v / deg_v to u."""
+    out = np.zeros((g.N, Y.shape[1]))
+    scale = np.zeros(g.N)
+    nz = g.deg > 0
+    scale[nz] = 1.0 / g.deg[nz]
+    np.add.at(out, g.col, Y[g.rows] * scale[g.rows, None])
+    return out
+
+
+# --------------------------------------------------------------------------
+# parameters
+# --------------------------------------------------------------------------
+def param_count(H0: int, H1: int, S: int) -> int:
+    """B1, W1 (H1 x H0 each), b1 (H1), B2, W2 (S x H1 each), b2 (S)."""
+    return 2 * H1 * H0 + H1 + 2 * S * H1 + S
+
+
+def unpack(theta: np.ndarray, H0: int, H1: int, S: int):
+    theta = np.asarray(theta, dtype=np.float64)
+    o = 0
+    Wcat1 = theta[o:o + H1 * 2 * H0].reshape(H1, 2 * H0); o += H1 * 2 * H0
+    b1 = theta[o:o + H1]; o += H1
+    Wcat2 = theta[o:o + S * 2 * H1].reshape(S, 2 * H1); o += S * 2 * H1
+    b2 = theta[o:o + S]; o += S
+    assert o == len(theta), "theta has the wrong length"
+    return dict(B1=Wcat1[:, :H0], W1=Wcat1[:, H0:], b1=b1,
+                B2=Wcat2[:, :H1], W2=Wcat2[:, H1:], b2=b2)
+
+
+def pack(B1, W1, b1, B2, W2, b2) -> np.ndarray:
+    return np.concatenate([np.concatenate([B1, W1], axis=1).ravel(), b1,
+                           np.concatenate([B2, W2], axis=1).ravel(), b2])
+
+
+# --------------------------------------------------------------------------
+# forward: two GCN layers (Eq. GCN), ReLU, sigmoid head of width S (App. C.1)
+# --------------------------------------------------------------------------
+def sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def forward(g: Graph, theta, X0, H0, H1, S):
+    p = unpack(theta, H0, H1, S)
+    X0 = np.asarray(X0, dtype=np.float64)
+    M1 = mean_aggregate(g, X0)
+    Z1 = X0 @ p["B1"].T + M1 @ p["W1"].T + p["b1"]
+    H1a = np.maximum(Z1, 0.0)
+    M2 = mean_aggregate(g, H1a)
+    Z2 = H1a @ p["B2"].T + M2 @ p["W2"].T + p["b2"]
+    P = sigmoid(Z2)
+    return dict(X0=X0, M1=M1, Z1=Z1, H1=H1a, M2=M2, Z2=Z2, P=P)
+
+
+# --------------------------------------------------------------------------
+# relaxed loss terms (Eq. CPRA-loss-function-GNN, -penalty, -variation)
+# --------------------------------------------------------------------------
+def shot_variance(P: np.ndarray) -> np.ndarray:
+    """VAR_s[P_is] per node i, population form (Notation section)."""
+    S = P.shape[1]
+    m = P.sum(axis=1) / S
+    return ((P - m[:, None]) ** 2).sum(axis=1) / S
+
+
+def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD):
+    """Per-shot cost_s, pen_s, ann_s and the shot-coupling Psi.
+
+    MIS    l = -sum_i p_i + lambda sum_{(i,j) in E} p_i p_j
+           cost_s = -sum_i P_is, pen_s = sum_{(i,j) in E} P_is P_js
+    MaxCut l = sum_{i<j} A_ij (2 p_i p_j - p_i - p_j); cost_s = l, pen_s = 0
+    ann_s  = sum_i 1 - (2 P_is - 1)^alpha
+    Psi    = -S sum_i STD_s[P_is]        (STD form, Eq. ...-variation)
+           = -S^2 sum_i VAR_s[P_is]      (VAR form, Prop. 3.2 left-hand side)
+    """
+    P = np.asarray(P, dtype=np.float64)
+    S = P.shape[1]
+    Pi, Pj = P[g.ei], P[g.ej]
+    if problem == MIS:
+        cost = -P.sum(axis=0)
+        pen = (Pi * Pj).sum(axis=0)
+    elif problem == MAXCUT:
+        cost = (g.ew[:, None] * (2.0 * Pi * Pj - Pi - Pj)).sum(axis=0)
+        pen = np.zeros(S)
+    else:
+        raise ValueError("problem")
+    ann = (1.0 - (2.0 * P - 1.0) ** alpha).sum(axis=0)
+    var = shot_variance(P)
+    if div_kind == DIV_STD:
+        psi = -S * np.sqrt(var).sum()
+    elif div_kind == DIV_VAR:
+        psi = -(S ** 2) * var.sum()
+    else:
+        raise ValueError("div_kind")
+    return dict(cost=cost, pen=pen, ann=ann, psi=psi)
+
+
+def total_loss(terms, lam, gamma, nu, problem):
+    lam = np.asarray(lam, dtype=np.float64)
+    base = terms["cost"].sum()
+    if problem == MIS:
+        base += (lam * terms["pen"]).sum()
+    return base + gamma * terms["ann"].sum() + nu * terms["psi"]
+
+
+def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD):
+    """dR/dP_is, analytic, with the edge list traversed once per edge."""
+    P = np.asarray(P, dtype=np.float64)
+    N, S = P.shape
+    G = np.zeros((N, S))
+    if problem == MIS:
+        lam = np.asarray(lam, dtype=np.float64)
+        G -= 1.0
+        np.add.at(G, g.ei, lam[None, :] * P[g.ej])
+        np.add.at(G, g.ej, lam[None, :] * P[g.ei])
+    else:
+        w = g.ew[:, None]
+        np.add.at(G, g.ei, w * (2.0 * P[g.ej] - 1.0))
+        np.add.at(G, g.ej, w * (2.0 * P[g.ei] - 1.0))
+    # gamma * d/dp [1 - (2p-1)^alpha] = -2 alpha gamma (2p-1)^(alpha-1)
+    G += -2.0 * alpha * gamma * (2.0 * P - 1.0) ** (alpha - 1)
+    if nu != 0.0:
+        m = P.sum(axis=1) / S
+        dev = P - m[:, None]
+        var = (dev ** 2).sum(axis=1) / S
+        if div_kind == DIV_STD:
+            # d/dP_is [-S sqrt(VAR_i)] = -(P_is - m_i) / sqrt(VAR_i)
+            gd = np.zeros_like(P)
+            nz = var > 0.0
+            gd[nz] = -dev[nz] / np.sqrt(var[nz])[:, None]
+        else:
+            # d/dP_is [-S^2 VAR_i] = -2 S (P_is - m_i)
+            gd = -2.0 * S * dev
+        G += nu * gd
+    return G
+
+
+# --------------------------------------------------------------------------
+# backward through the GNN (chain rule of Eq. GCN twice)
+# --------------------------------------------------------------------------
+def backward(g: Graph, theta, cache, G_P, H0, H1, S):
+    p = unpack(theta, H0, H1, S)
+    P = cache["P"]
+    G_Z2 = G_P * P * (1.0 - P)                    # sigmoid'
+    dB2 = G_Z2.T @ cache["H1"]
+    dW2 = G_Z2.T @ cache["M2"]
+    db2 = G_Z2.sum(axis=0)
+    G_H1 = G_Z2 @ p["B2"] + mean_aggregate_adjoint(g, G_Z2 @ p["W2"])
+    G_Z1 = G_H1 * (cache["Z1"] > 0.0)             # ReLU'
+    dB1 = G_Z1.T @ cache["X0"]
+    dW1 = G_Z1.T @ cache["M1"]
+    db1 = G_Z1.sum(axis=0)
+    G_X0 = G_Z1 @ p["B1"] + mean_aggregate_adjoint(g, G_Z1 @ p["W1"])
+    return dict(theta=pack(dB1, dW1, db1, dB2, dW2, db2), X0=G_X0,
+                G_Z2=G_Z2, G_Z1=G_Z1)
+
+
+# --------------------------------------------------------------------------
+# optimiser and annealing schedule
+# --------------------------------------------------------------------------
+def adam(theta, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """One Adam step (Kingma & Ba), t >= 1; wd > 0 adds AdamW's decoupled
+    decay theta <- theta (1 - lr wd) before the moment step."""
+    theta = np.asarray(theta, np.float64)
+    m = np.asarray(m, np.float64)
+    v = np.asarray(v, np.float64)
+    grad = np.asarray(grad, np.float64)
+    if wd != 0.0:
+        theta = theta * (1.0 - lr * wd)
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    theta = theta - lr * mhat / (np.sqrt(vhat) + eps)
+    return theta, m, v
+
+
+def gamma_schedule(t, T, gamma0, gamma1):
+    """Linear anneal gamma_t = gamma0 + (gamma1 - gamma0) t / (T - 1)."""
+    if T <= 1:
+        return gamma1
+    return gamma0 + (gamma1 - gamma0) * min(t, T - 1) / (T - 1)
+
+
+# --------------------------------------------------------------------------
+# rounding and integer evaluation (App. C.2, Table objective-functions)
+# --------------------------------------------------------------------------
+def round_solutions(P) -> np.ndarray:
+    """x_is = 0 if P_is <= 0.5 else 1."""
+    return (np.asarray(P) > 0.5).astype(np.int64)
+
+
+def integer_eval(g: Graph, X, lam, problem):
+    """Per shot: objective (MIS set size / MaxCut cut size), violations
+    (MIS: edges with both ends selected; MaxCut: 0), qubo value l(x), and
+    the pairwise Hamming sum sum_{s<l} d_H(x_s, x_l)."""
+    X = np.asarray(X, dtype=np.int64)
+    N, S = X.shape
+    Xi, Xj = X[g.ei], X[g.ej]
+    if problem == MIS:
+        obj = X.sum(axis=0)
+        viol = (Xi * Xj).sum(axis=0)
+        qubo = -obj.astype(np.float64) + np.asarray(lam, np.float64) * viol
+    else:
+        obj = (Xi != Xj).sum(axis=0)
+        viol = np.zeros(S, dtype=np.int64)
+        qubo = -(g.ew[:, None] * (Xi != Xj)).sum(axis=0)
+    k = X.sum(axis=1)
+    pair_hamming = int((k * (S - k)).sum())
+    return dict(objective=obj.astype(np.int64), violations=viol.astype(np.int64),
+                qubo=qubo.astype(np.float64), pair_hamming=pair_hamming)
+
+
+def pack_bits(X) -> np.ndarray:
+    """Rounded solutions as uint32 words: bit (s mod 32) of word s // 32 of
+    row i is x_is.  Shape N x ceil(S/32)."""
+    X = np.asarray(X, dtype=np.uint64)
+    N, S = X.shape
+    W = (S + 31) // 32
+    out = np.zeros((N, W), dtype=np.uint64)
+    for s in range(S):
+        out[:, s // 32] |= X[:, s] << np.uint64(s % 32)
+    return out.astype(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# one full training step
+# --------------------------------------------------------------------------
+def step(g: Graph, theta, X0, cfg, t, adam_state=None):
+    """One CPRA step at iteration t (1-based for Adam bias correction).
+
+    cfg keys: H0, H1, S, problem, alpha, lam (S), gamma, nu, div_kind,
+    lr, beta1, beta2, eps, wd, train_embedding.
+    adam_state: dict(m_theta, v_theta, m_X0, v_X0) or None (zeros)."""
+    H0, H1, S = cfg["H0"], cfg["H1"], cfg["S"]
+    cache = forward(g, theta, X0, H0, H1, S)
+    P = cache["P"]
+    terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"])
+    L = total_loss(terms, cfg["lam"], cfg["gamma"], cfg["nu"], cfg["problem"])
+    G_P = grad_P(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["gamma"],
+                 cfg["nu"], cfg["div_kind"])
+    grads = backward(g, theta, cache, G_P, H0, H1, S)
+    if adam_state is None:
+        adam_state = dict(m_theta=np.zeros(len(theta)), v_theta=np.zeros(len(theta)),
+                          m_X0=np.zeros(np.shape(X0)), v_X0=np.zeros(np.shape(X0)))
+    hp = dict(lr=cfg["lr"], beta1=cfg["beta1"], beta2=cfg["beta2"], eps=cfg["eps"],
+              wd=cfg["wd"])
+    th1, mt, vt = adam(theta, adam_state["m_theta"], adam_state["v_theta"],
+                       grads["theta"], t, **hp)
+    if cfg.get("train_embedding", True):
+        x1, mx, vx = adam(X0, adam_state["m_X0"], adam_state["v_X0"], grads["X0"], t, **hp)
+    else:
+        x1 = np.asarray(X0, np.float64)
+        mx = np.asarray(adam_state["m_X0"], np.float64)
+        vx = np.asarray(adam_state["v_X0"], np.float64)
+    X = round_solutions(P)
+    ev = integer_eval(g, X, cfg["lam"], cfg["problem"])
+    return dict(cache=cache, P=P, terms=terms, loss=L, G_P=G_P, grads=grads,
+                theta_next=th1, X0_next=x1,
+                adam_next=dict(m_theta=mt, v_theta=vt, m_X0=mx, v_X0=vx),
+                X=X, eval=ev)
