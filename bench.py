@@ -1,0 +1,372 @@
+"""Benchmark of one CPRA training step on GB300 (edge*shot*steps/s).
+
+Workload (default): MIS on a seeded random 5-regular graph with N = 10^6
+nodes (nnz = 2|E| = 5*10^6), S = 256 penalty shots with lambda_s log-spaced
+0.5..10, a two-layer GCN of width 128 with BF16 dense layers (FP32 loss,
+Adam and rounding).  A step is the whole hot path: forward, fused SpMM +
+loss, adjoint, Adam, rounding and exact integer evaluation of all shots.
+Inputs are larger than L2 (P alone is N*S*4 = 1.0 GB), so no L2 flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+prints one JSON line.  The reference arm times the FP64 CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+if "reference" in sys.argv:
+    # the CPU reference arm runs single-threaded so its core count is exact
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+from paper_2402_02190_gb300 import inputs as I  # noqa: E402
+
+METRIC = "edge·shot·steps/s"
+
+WORKLOADS = {
+    # name: (graph, N, degree, seed, problem, S, H, lambda, nu, precision)
+    "mis_rrg5_n1e6_s256_h128_bf16": dict(graph="rrg", N=10**6, d=5, seed=5, problem=0, S=256,
+                                         H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
+                                         div=0),
+    "mis_rrg5_n1e6_s256_h128_fp32": dict(graph="rrg", N=10**6, d=5, seed=5, problem=0, S=256,
+                                         H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=0,
+                                         div=0),
+    "mis_rrg20_n1e4_s100_h256_bf16": dict(graph="rrg", N=10**4, d=20, seed=2, problem=0, S=100,
+                                          H=256, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
+                                          div=0),
+    "maxcut_er10_n1e5_s64_h128_bf16": dict(graph="er", N=10**5, d=10, seed=3, problem=1, S=64,
+                                           H=128, lam=None, nu=0.1, precision=1, div=1),
+    "mis_rrg3_n100_s8_h16_fp32": dict(graph="rrg", N=100, d=3, seed=1, problem=0, S=8, H=16,
+                                      lam=("lin", 1.0, 8.0), nu=0.0, precision=0, div=0),
+}
+DEFAULT_WORKLOAD = "mis_rrg5_n1e6_s256_h128_bf16"
+# Bounded CPU sample for the oracle: same degree, width and shots, N / 100.
+CPU_SAMPLE_N = 10**4
+
+
+def make_graph(w):
+    if w["graph"] == "rrg":
+        return I.random_regular_graph(w["N"], w["d"], w["seed"])
+    return I.erdos_renyi_graph(w["N"], w["d"] / (w["N"] - 1), w["seed"])
+
+
+def make_lambda(w):
+    if w["lam"] is None:
+        return None
+    kind, lo, hi = w["lam"]
+    return I.lambda_geomspace(lo, hi, w["S"]) if kind == "geom" else I.lambda_linspace(lo, hi, w["S"])
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
+    if not os.path.exists(p):
+        return None
+    fields = {}
+    for line in open(p):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    src = os.path.join(ROOT, "paper_2402_02190_gb300", "csrc", fields.get("source", "k_loss.cu"))
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def loss_kernel_bytes(N, nnz, S, g_bytes):
+    """Algorithmic bytes of one fused SpMM + loss launch: neighbour-row
+    gathers nnz*S*4, own P row N*S*4, G write N*S*g_bytes, CSR 4(N+1)+4nnz,
+    rounded bits N*ceil(S/32)*4."""
+    return nnz * S * 4 + N * S * 4 + N * S * g_bytes + 4 * (N + 1) + 4 * nnz + N * ((S + 31) // 32) * 4
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_steps(w, n_nodes, steps, seed=0):
+    """Runs `steps` FP64 oracle steps on the bounded sample; returns
+    (seconds, nnz, S)."""
+    from oracle import cpra_oracle as O
+    ws = dict(w, N=n_nodes)
+    rp, col = make_graph(ws)
+    g = O.Graph(rp, col)
+    S, H = w["S"], w["H"]
+    lam = make_lambda(w)
+    theta, X0 = I.seeded_params(n_nodes, H, H, S, seed=seed + 1)
+    cfg = dict(H0=H, H1=H, S=S, problem=w["problem"], alpha=2,
+               lam=(np.zeros(S) if lam is None else lam.astype(np.float64)), gamma=-1.0,
+               nu=w["nu"], div_kind=w["div"], lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0,
+               train_embedding=True)
+    state = None
+    th, x0 = theta.astype(np.float64), X0.astype(np.float64)
+    t0 = time.perf_counter()
+    for t in range(steps):
+        out = O.step(g, th, x0, cfg, t=t + 1, adam_state=state)
+        th, x0, state = out["theta_next"], out["X0_next"], out["adam_next"]
+    return time.perf_counter() - t0, int(rp[-1]), S
+
+
+def cpu_baseline_child(argv):
+    """Child process (single-threaded BLAS): times the oracle on the bounded
+    sample for about `budget` seconds and prints one JSON line."""
+    wname, budget = argv[0], float(argv[1])
+    w = WORKLOADS[wname]
+    n = min(CPU_SAMPLE_N, w["N"])
+    dt, nnz, S = oracle_steps(w, n, 1)
+    steps = max(1, int(budget / max(dt, 1e-3)))
+    dt2, nnz, S = oracle_steps(w, n, steps)
+    print(json.dumps({"value": nnz * S * steps / dt2, "steps": steps, "seconds": dt2,
+                      "nnz": nnz, "N": n}))
+
+
+def run_cpu_baseline(wname, budget=15.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", wname,
+                        str(budget)], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip()[-200:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    w = WORKLOADS[wname]
+    return {"value": d["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": (f"{d['steps']} FP64 oracle step(s) on a {w['graph']} graph N={d['N']} "
+                       f"(degree {w['d']}, nnz={d['nnz']}), S={w['S']}, H={w['H']}, same problem; "
+                       f"{d['seconds']:.1f} s single-threaded numpy")}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_2402_02190_gb300 import cpra
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    rp, col = make_graph(w)
+    N, nnz, S, H = w["N"], int(rp[-1]), w["S"], w["H"]
+    lam = make_lambda(w)
+    kw = dict(problem=w["problem"], S=S, H0=H, H1=H, precision=w["precision"], nu=w["nu"],
+              diversity_kind=w["div"], gamma0=-2.0, gamma1=0.1,
+              schedule_steps=args.warmup + args.steps, seed=1 + rank)
+
+    solver = cpra.Solver(rp, col, lam=lam, **kw)
+    stream = solver.stream          # the stream every library kernel is launched on
+    for t in range(args.warmup):
+        solver.step(t)
+    torch.cuda.synchronize()
+    cpra.cpra_profile_enable(solver.ctx, True)
+    cpra.cpra_profile_read(solver.ctx)          # reset counters
+    launches0 = solver.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for t in range(args.warmup, args.warmup + args.steps):
+            solver.step(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = cpra.cpra_profile_read(solver.ctx)
+    launches = solver.launches - launches0
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    solver.close()
+    del solver
+    torch.cuda.synchronize()
+
+    # end to end through the public API with host buffers: init from the host
+    # CSR, every step returns its loss terms to the host, final evaluation
+    # copied back.
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = cpra.Solver(rp, col, lam=lam, **kw)
+    for t in range(args.steps):
+        s2.step(t, want_terms=True)
+    rec, ham, _ = s2.round_eval()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    h2d = (8 * (N + 1) + 4 * nnz + (4 * S if lam is not None else 0)) / args.steps
+    d2h = (3 * S + 1) * 4 + (S * 24 + 8) / args.steps
+
+    value = world * nnz * S * args.steps / (ms / 1e3)
+    peak, peak_src = read_peaks()
+    loss_ms, loss_n = prof.get("loss_fused", (0.0, 0))
+    g_bytes = 2 if w["precision"] == 1 else 4
+    alg = loss_kernel_bytes(N, nnz, S, g_bytes)
+    achieved = alg / (loss_ms / loss_n / 1e3) / 1e9 if loss_n else None
+    traffic = ncu_traffic("loss_fused", args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if w["precision"] == 1 else "f32",
+        "dtype_detail": ("dense layers bf16 operands / fp32 accumulation; loss, Adam, rounding fp32; "
+                         "objective reduction int64/fp64") if w["precision"] == 1 else "all fp32",
+        "data": "synthetic (seeded random graph, random-init GCN)",
+        "config": {"workload": args.workload, "graph": f"{w['graph']} degree {w['d']}", "N": N,
+                   "nnz": nnz, "S": S, "H0": H, "H1": H,
+                   "problem": ["MIS", "MaxCut"][w["problem"]], "nu": w["nu"],
+                   "precision": ["fp32", "bf16"][w["precision"]], "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 (P = {N * S * 4 / 1e9:.2f} GB), no flush"},
+        "roofline": {"kernel": "loss_fused", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "alg_bytes_per_launch": alg, "avg_ms": loss_ms / loss_n if loss_n else None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": nnz * S * args.steps / e2e_s, "unit": METRIC,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "seconds": e2e_s},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "kernels_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / args.steps)
+                                for k, v in prof.items() if v[1]},
+        "best_eval": {"max_objective_feasible": int(max(
+            [r["objective"] for r in rec if r["violations"] == 0] or [-1]))},
+    }
+    if rank == 0:
+        line["cpu_baseline"] = run_cpu_baseline(args.workload) if not args.no_cpu else None
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    n = min(CPU_SAMPLE_N, w["N"])
+    for _ in range(args.warmup):
+        oracle_steps(w, n, 1)
+    dt, nnz, S = oracle_steps(w, n, args.steps)
+    value = nnz * S * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
+    sample = (f"{args.steps} FP64 oracle steps on a {w['graph']} graph N={n} (degree {w['d']}, "
+              f"nnz={nnz}), S={S}, H={w['H']}: the default workload at N/100")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample_N": n},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-baseline-child":
+        cpu_baseline_child(sys.argv[2:])
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * cpra.h -- C ABI of the GB300 (sm_103a) implementation of one training step
+ * of CPRA, the continuous parallel relaxation annealing solver of Ichikawa &
+ * Iwashita, "Continuous Parallel Relaxation for Finding Diverse Solutions in
+ * Combinatorial Optimization Problems".
+ *
+ * One step = GNN forward (Eq. GCN, App. B.1, two layers as in App. C.1)
+ *          -> S relaxed QUBO losses with the annealing term and, optionally,
+ *             the shot-diversity term (Eq. CPRA-loss-function-GNN-penalty and
+ *             Eq. CPRA-loss-function-GNN-variation)
+ *          -> hand-written adjoint -> Adam
+ *          -> rounding x = 1[P > 0.5] (App. C.2) and integer evaluation of all
+ *             S shots (MIS / MaxCut objectives of Table objective-functions).
+ *
+ * Conventions for every entry point
+ *   - Plain C types only.  "host" pointers are ordinary CPU memory; "device"
+ *     pointers are CUDA global memory of the current device.
+ *   - Host input arrays are read during the call and never retained; the
+ *     caller keeps ownership.  Outputs go to caller-allocated buffers.
+ *   - No entry point aborts or throws.  Errors are returned as cpra_status;
+ *     cpra_last_error() gives a message for context calls.
+ *   - Graph input: symmetric CSR, rowptr int64[N+1] with rowptr[0] = 0,
+ *     col int32[nnz] with 0 <= col < N, strictly increasing within each row
+ *     (no duplicates), no self-loops, and (i,j) present iff (j,i) present.
+ *     nnz = 2|E| must be < 2^31.  Isolated nodes are allowed (their mean
+ *     aggregation is 0).  Anything else is CPRA_EINVAL.
+ *   - Matrices are row-major.  P and the shot-indexed buffers use a row
+ *     stride S_pad = round_up(S, 16) elements; pad columns are never read as
+ *     data.
+ */
+#ifndef CPRA_H
+#define CPRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CPRA_API __attribute__((visibility("default")))
+#else
+#define CPRA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CPRA_OK = 0,
+  CPRA_EINVAL = 1,   /* bad argument, graph or configuration              */
+  CPRA_ENOMEM = 2,   /* device allocation failed or exceeds mem_cap_bytes  */
+  CPRA_ECUDA = 3,    /* a CUDA runtime / driver call failed                */
+  CPRA_ENUMERIC = 4, /* non-finite loss term detected                      */
+  CPRA_ETIMEOUT = 5, /* a bounded device-side wait gave up                 */
+  CPRA_ESTATE = 6    /* state blob does not match this context             */
+} cpra_status;
+
+enum { CPRA_MIS = 0, CPRA_MAXCUT = 1 };               /* Table objective-functions */
+enum { CPRA_FP32 = 0, CPRA_BF16 = 1 };                /* dense-layer arithmetic   */
+enum { CPRA_DIV_STD = 0, CPRA_DIV_VAR = 1 };          /* Psi form                 */
+
+/* Configuration.  cpra_config_default() fills every field. */
+typedef struct cpra_config {
+  int32_t problem;          /* CPRA_MIS or CPRA_MAXCUT                           */
+  int32_t S;                /* shots = columns of P, 1..1024                      */
+  int32_t H0;               /* node-embedding width (multiple of 16, <= 1024)    */
+  int32_t H1;               /* hidden width (multiple of 16, <= 1024)            */
+  int32_t alpha;            /* even exponent of the annealing term, >= 2          */
+  int32_t precision;        /* CPRA_FP32: all FP32; CPRA_BF16: dense layers BF16
+                               on tensor cores with FP32 accumulation             */
+  int32_t recompute;        /* 1: layer-1 activations are recomputed in backward  */
+  int32_t train_embedding;  /* 1: node embeddings h^0 are trained (default)       */
+  int32_t diversity_kind;   /* CPRA_DIV_STD (Eq. ...-variation) or CPRA_DIV_VAR   */
+  int32_t reserved0;
+  const float* lambda;      /* host [S], penalty lambda_s per shot (MIS); copied
+                               at init; may be NULL for MaxCut                     */
+  float nu;                 /* diversity weight (0 disables Psi)                  */
+  float gamma0, gamma1;     /* annealing: gamma_t linear from gamma0 to gamma1    */
+  int64_t schedule_steps;   /*   over t = 0 .. schedule_steps-1                   */
+  float lr, beta1, beta2, eps;
+  float weight_decay;       /* 0: Adam; > 0: decoupled AdamW decay                */
+  uint64_t seed;            /* parameter / embedding initialisation              */
+  uint64_t mem_cap_bytes;   /* 0: none; else init fails with CPRA_ENOMEM when the
+                               device workspace would exceed it                    */
+} cpra_config;
+
+/* Result of rounding one shot (App. C.2) and evaluating it exactly. */
+typedef struct cpra_shot_eval {
+  int64_t objective;   /* MIS: |{i : x_i = 1}|;  MaxCut: number of cut edges   */
+  int64_t violations;  /* MIS: edges with both ends in the set; MaxCut: 0      */
+  double qubo;         /* l(x): MIS -objective + lambda_s * violations;
+                          MaxCut -objective                                     */
+} cpra_shot_eval;
+
+typedef struct cpra_ctx cpra_ctx;
+
+/* Fills *cfg with defaults: MIS, S = 8, H0 = H1 = 16, alpha = 2, FP32,
+   recompute 0, train_embedding 1, DIV_STD, nu = 0, gamma -2 -> 0.1 over 3000
+   steps, Adam lr 1e-3, betas (0.9, 0.999), eps 1e-8, wd 0, seed 1. */
+CPRA_API void cpra_config_default(cpra_config* cfg);
+
+/* Number of trainable GNN parameters excluding node embeddings:
+   2*H1*H0 + H1 + 2*S*H1 + S (self weight, neighbour weight and bias per
+   layer; this reproduces the counts printed in the Experiments section's
+   tables, e.g. 5,083,076 for H0 = H1 = 1584, S = 20). */
+CPRA_API int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S);
+
+/* Device bytes a context needs for this graph size and configuration
+   (0 if the configuration is invalid). */
+CPRA_API size_t cpra_workspace_bytes(int64_t N, int64_t nnz, const cpra_config* cfg);
+
+/* Creates a context: validates and uploads the graph (host CSR, see
+   conventions; w must be NULL -- unit weights), copies cfg and lambda, and
+   initialises theta ~ U(+-1/sqrt(fan_in)) and h^0 ~ N(0,1) from cfg->seed.
+   dev_workspace: device buffer of >= cpra_workspace_bytes() bytes owned by
+   the caller for the context's lifetime, or NULL to let the library
+   allocate (and free in cpra_destroy).  cuda_stream: cudaStream_t to order
+   all work on, or NULL for a stream owned by the context.  On failure *out
+   is NULL. */
+CPRA_API cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
+                            const int32_t* col, const float* w,
+                            const cpra_config* cfg, void* dev_workspace,
+                            size_t workspace_bytes, void* cuda_stream);
+
+/* One training step at schedule index t (gamma_t = gamma0 + (gamma1 -
+   gamma0) * t / (schedule_steps - 1), clamped).  Runs forward, loss, adjoint,
+   Adam (bias-corrected with the context's own step counter, which this call
+   increments) and the rounding/evaluation of the P of this step's forward.
+   loss_terms_out: host float[3S+1] receiving cost_s (S), pen_s (S), ann_s (S)
+   and Psi, or NULL.  Asynchronous on the context stream when NULL; otherwise
+   synchronises and returns CPRA_ENUMERIC if a term is not finite. */
+CPRA_API cpra_status cpra_step(cpra_ctx* ctx, int64_t t, float* loss_terms_out);
+
+/* Copies the evaluation of the most recent cpra_step (or, before any step,
+   of a fresh forward pass) to the host.  out: host [S]; pair_hamming_sum:
+   host int64 receiving sum_i k_i (S - k_i) = sum_{s<l} d_H(x_s, x_l)
+   (Prop. 3.2), or NULL; x_bits_out: host uint32 [N][ceil(S/32)] with bit
+   (s mod 32) of word s/32 = x_is, or NULL.  Synchronises. */
+CPRA_API cpra_status cpra_round_eval(cpra_ctx* ctx, cpra_shot_eval* out,
+                            int64_t* pair_hamming_sum, uint32_t* x_bits_out);
+
+/* Runs `steps` steps starting at schedule index 0 and, every eval_every
+   steps and after the last, tracks per shot the best evaluation: MIS the
+   largest objective with violations == 0 (objective -1 if none seen),
+   MaxCut the largest cut.  best_out: host [S]; best_step_out: host [S] step
+   index of that evaluation (or -1), may be NULL. */
+CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every,
+                       cpra_shot_eval* best_out, int64_t* best_step_out);
+
+/* Tensors a context exposes for checkpoints, tests and inspection. */
+enum {
+  CPRA_T_THETA = 0,     /* float [param_count] flat: Wcat1=[B1|W1] (H1 x 2H0),
+                           b1 (H1), Wcat2=[B2|W2] (S x 2H1), b2 (S)          */
+  CPRA_T_THETA_M = 1,   /* float [param_count] Adam first moment              */
+  CPRA_T_THETA_V = 2,   /* float [param_count] Adam second moment             */
+  CPRA_T_EMB = 3,       /* float [N x H0] node embeddings h^0 (FP32 master)   */
+  CPRA_T_EMB_M = 4,     /* float [N x H0]                                     */
+  CPRA_T_EMB_V = 5,     /* float [N x H0]                                     */
+  CPRA_T_GRAD = 6,      /* float [param_count] dR/dtheta of the last step     */
+  CPRA_T_EMB_GRAD = 7,  /* float [N x H0] dR/dh^0 of the last step            */
+  CPRA_T_P = 8,         /* float [N x S] P of the last forward                */
+  CPRA_T_GZ2 = 9,       /* float [N x S] dR/dZ2 of the last step (upcast)     */
+  CPRA_T_STEP = 10,     /* int64 [1] Adam step counter                        */
+  CPRA_T_TERMS = 11,    /* float [3S+1] loss terms of the last step           */
+  CPRA_T_COUNT_ = 12
+};
+
+/* Size in bytes of tensor `which` (0 if unknown). */
+CPRA_API size_t cpra_tensor_bytes(const cpra_ctx* ctx, int32_t which);
+/* Copies tensor `which` to / from host memory of exactly nbytes.
+   Synchronises.  Setting CPRA_T_THETA or CPRA_T_EMB refreshes the BF16
+   shadows used by the dense layers. */
+CPRA_API cpra_status cpra_get_tensor(cpra_ctx* ctx, int32_t which, void* host, size_t nbytes);
+CPRA_API cpra_status cpra_set_tensor(cpra_ctx* ctx, int32_t which, const void* host, size_t nbytes);
+
+/* Checkpoint: opaque blob with theta, its Adam moments, the embeddings and
+   their moments, and the step counter.  With buf == NULL, *nbytes receives
+   the size.  cpra_set_state checks the header against the context
+   (CPRA_ESTATE on mismatch).  Resuming reproduces an uninterrupted run
+   bit for bit. */
+CPRA_API cpra_status cpra_get_state(cpra_ctx* ctx, void* buf, size_t* nbytes);
+CPRA_API cpra_status cpra_set_state(cpra_ctx* ctx, const void* buf, size_t nbytes);
+
+/* host [N x S] float: P of the last forward. */
+CPRA_API cpra_status cpra_get_P(cpra_ctx* ctx, float* host_NxS);
+
+CPRA_API int64_t cpra_param_count(const cpra_ctx* ctx);
+/* Kernel launches issued by this context so far. */
+CPRA_API int64_t cpra_launch_count(const cpra_ctx* ctx);
+
+/* Per-kernel device timing.  While enabled, each step records CUDA events
+   around its kernels on the context stream.  cpra_profile_read synchronises
+   and returns, per kernel id (see cpra_kernel_name), the summed device
+   milliseconds and the launch count since the last read, then resets them. */
+CPRA_API void cpra_profile_enable(cpra_ctx* ctx, int on);
+CPRA_API int32_t cpra_profile_read(cpra_ctx* ctx, double* ms_out, int64_t* launches_out,
+                          int32_t n_ids);
+CPRA_API const char* cpra_kernel_name(int32_t id);
+
+/* Message of the last error on ctx; with ctx == NULL, the message of the
+   last failed cpra_init_graph on the calling thread. */
+CPRA_API const char* cpra_last_error(const cpra_ctx* ctx);
+CPRA_API const char* cpra_status_string(cpra_status s);
+CPRA_API void cpra_destroy(cpra_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Op-level entry points on caller-owned DEVICE memory, ordered on
+ * `cuda_stream` (NULL = legacy default stream).  They allocate nothing.
+ * ---------------------------------------------------------------------- */
+
+/* Fused SpMM + relaxed loss (the step's loss stage).  For every node i and
+ * shot s < S, with Q = A P (A the unit-weight adjacency of the CSR):
+ *   MIS:    cost_s = -sum_i P_is,  pen_s = 1/2 sum_i P_is Q_is
+ *           dR/dP_is = -1 + lambda_s Q_is + ...
+ *   MaxCut: cost_s = sum_i P_is Q_is - sum_i deg_i P_is,  pen_s = 0
+ *           dR/dP_is = 2 Q_is - deg_i + ...
+ *   both:   ann_s = sum_i 1 - (2P_is - 1)^alpha,
+ *           ... - 2 alpha gamma (2P_is - 1)^(alpha-1) + nu dPsi/dP_is
+ *   Psi = -S sum_i STD_s(P_i.)  (DIV_STD; gradient 0 on rows with VAR = 0)
+ *       = -S^2 sum_i VAR_s(P_i.) (DIV_VAR)
+ * (Eq. CPRA-loss-function-GNN-penalty / -variation, Table
+ * objective-functions.)  Q is never stored.
+ *   rowptr, col : device int32 [N+1], [nnz]
+ *   P           : device float [N x ldp], ldp >= S, ldp % 4 == 0
+ *   lambda      : device float [S] (MIS; ignored for MaxCut, may be NULL)
+ *   grad_kind   : 0 -> G = dR/dP * P (1 - P)  (= dR/dZ2 under a sigmoid head)
+ *                 1 -> G = dR/dP
+ *   G           : device float [N x ldg], ldg >= S, ldg % 4 == 0; columns
+ *                 S..ldg-1 are written 0
+ *   x_bits      : device uint32 [N x ceil(S/32)] rounded P (x = P > 0.5f),
+ *                 or NULL
+ *   terms       : device float [4S+1]: cost_s, pen_s, ann_s, Psi, then
+ *                 sum_i G_is per shot (S)
+ *   scratch     : device, >= cpra_op_loss_scratch_bytes(N, S) bytes
+ * Results are deterministic (fixed-order reductions). */
+CPRA_API size_t cpra_op_loss_scratch_bytes(int64_t N, int32_t S);
+CPRA_API cpra_status cpra_op_loss(int64_t N, int32_t S, const int32_t* rowptr,
+                         const int32_t* col, const float* P, int64_t ldp,
+                         const float* lambda, int32_t problem, int32_t alpha,
+                         float gamma, float nu, int32_t diversity_kind,
+                         int32_t grad_kind, float* G, int64_t ldg,
+                         uint32_t* x_bits, float* terms, void* scratch,
+                         size_t scratch_bytes, void* cuda_stream);
+
+/* Rounding + exact integer evaluation of S shots from P (App. C.2):
+ * x_is = 1[P_is > 0.5f]; per shot objective / violations / qubo as in
+ * cpra_shot_eval (qubo reduced in FP64), and sum_i k_i (S - k_i).
+ *   P        : device float [N x ldp]
+ *   x_bits   : device uint32 [N x ceil(S/32)] work/output buffer
+ *   lambda   : device float [S] (MIS) or NULL
+ *   out      : device cpra_shot_eval [S]
+ *   pair_hamming : device int64 [1]
+ *   counters : device, >= cpra_op_round_eval_scratch_bytes(S) bytes
+ * Bit-exact and deterministic (integer reductions). */
+CPRA_API size_t cpra_op_round_eval_scratch_bytes(int32_t S);
+CPRA_API cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr,
+                               const int32_t* col, const float* P, int64_t ldp,
+                               const float* lambda, int32_t problem,
+                               uint32_t* x_bits, cpra_shot_eval* out,
+                               int64_t* pair_hamming, void* counters,
+                               size_t counters_bytes, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPRA_H */

@@ -30,6 +30,9 @@ Readings of points the paper leaves open:
     alpha = 2 case only);
   * every undirected edge counted once in the MIS penalty and the MaxCut sum;
   * Psi gradient is zero on rows whose variance across shots is exactly 0;
+  * the ReLU sign is a discrete decision taken from floating point: for the
+    BF16 form it is taken on bfloat16-rounded operands, as the kernels do
+    (``relu_decision="bf16"``); every value stays float64;
   * the optional "VAR" diversity form Psi_var = -S^2 sum_i VAR_s[P_is] is the
     left-hand side of Prop. 3.2 (negated);
   * parameters: one self weight B^k, one neighbour weight W^k and one bias
@@ -132,16 +135,39 @@ def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
 
-def forward(g: Graph, theta, X0, H0, H1, S):
+def bf16_round(x) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even), returned
+    as float64.  bfloat16 keeps the float32 sign and exponent and the top 7
+    mantissa bits."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(g: Graph, theta, X0, H0, H1, S, relu_decision=None):
+    """relu_decision: None decides the ReLU sign 1[Z1 > 0] on the float64
+    Z1; "bf16" decides it on Z1 recomputed from bfloat16-rounded operands
+    (X0, the neighbour mean and the weights), the precision in which the
+    BF16 form's kernels take that decision.  All values stay float64."""
     p = unpack(theta, H0, H1, S)
     X0 = np.asarray(X0, dtype=np.float64)
     M1 = mean_aggregate(g, X0)
     Z1 = X0 @ p["B1"].T + M1 @ p["W1"].T + p["b1"]
-    H1a = np.maximum(Z1, 0.0)
+    if relu_decision is None:
+        on = Z1 > 0.0
+    elif relu_decision == "bf16":
+        xb = bf16_round(X0)
+        mb = bf16_round(mean_aggregate(g, xb))
+        zd = xb @ bf16_round(p["B1"]).T + mb @ bf16_round(p["W1"]).T + p["b1"]
+        on = zd > 0.0
+    else:
+        raise ValueError("relu_decision")
+    H1a = np.where(on, Z1, 0.0)
     M2 = mean_aggregate(g, H1a)
     Z2 = H1a @ p["B2"].T + M2 @ p["W2"].T + p["b2"]
     P = sigmoid(Z2)
-    return dict(X0=X0, M1=M1, Z1=Z1, H1=H1a, M2=M2, Z2=Z2, P=P)
+    return dict(X0=X0, M1=M1, Z1=Z1, relu_on=on, H1=H1a, M2=M2, Z2=Z2, P=P)
 
 
 # --------------------------------------------------------------------------
@@ -237,7 +263,7 @@ def backward(g: Graph, theta, cache, G_P, H0, H1, S):
     dW2 = G_Z2.T @ cache["M2"]
     db2 = G_Z2.sum(axis=0)
     G_H1 = G_Z2 @ p["B2"] + mean_aggregate_adjoint(g, G_Z2 @ p["W2"])
-    G_Z1 = G_H1 * (cache["Z1"] > 0.0)             # ReLU'
+    G_Z1 = G_H1 * cache["relu_on"]                # ReLU'
     dB1 = G_Z1.T @ cache["X0"]
     dW1 = G_Z1.T @ cache["M1"]
     db1 = G_Z1.sum(axis=0)
@@ -324,7 +350,7 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
     lr, beta1, beta2, eps, wd, train_embedding.
     adam_state: dict(m_theta, v_theta, m_X0, v_X0) or None (zeros)."""
     H0, H1, S = cfg["H0"], cfg["H1"], cfg["S"]
-    cache = forward(g, theta, X0, H0, H1, S)
+    cache = forward(g, theta, X0, H0, H1, S, cfg.get("relu_decision"))
     P = cache["P"]
     terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"])
     L = total_loss(terms, cfg["lam"], cfg["gamma"], cfg["nu"], cfg["problem"])

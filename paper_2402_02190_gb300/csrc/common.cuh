@@ -1,0 +1,131 @@
+// Device-side helpers shared by the CPRA kernels (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cpra {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(bf16 x) { return __bfloat162float(x); }
+
+template <typename T> __device__ __forceinline__ T from_f(float x);
+template <> __device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ bf16 from_f<bf16>(float x) { return __float2bfloat16_rn(x); }
+
+// Number of T elements in one 16-byte vector.
+template <typename T> struct V16 { static constexpr int n = 16 / (int)sizeof(T); };
+
+// Load one 16-byte vector of T (16-byte aligned) and widen to float.
+__device__ __forceinline__ void load16(const float* p, float* out) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+__device__ __forceinline__ void load16(const bf16* p, float* out) {
+  uint4 v = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
+    float2 f = __bfloat1622float2(h);
+    out[2 * k] = f.x;
+    out[2 * k + 1] = f.y;
+  }
+}
+// Read-only, no-L1-allocate variants for gathered rows.
+__device__ __forceinline__ uint4 ldg_nc16(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void widen(const uint4& v, float* out, const float*) {
+  out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
+  out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
+}
+__device__ __forceinline__ void widen(const uint4& v, float* out, const bf16*) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
+    float2 f = __bfloat1622float2(h);
+    out[2 * k] = f.x;
+    out[2 * k + 1] = f.y;
+  }
+}
+
+// Store N floats (N*sizeof(T) a multiple of 8 bytes, aligned) as T.
+template <int N>
+__device__ __forceinline__ void storeN(float* p, const float* v) {
+#pragma unroll
+  for (int k = 0; k < N; k += 4)
+    *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+}
+template <int N>
+__device__ __forceinline__ void storeN(bf16* p, const float* v) {
+  if constexpr (N % 8 == 0) {
+#pragma unroll
+    for (int k = 0; k < N; k += 8) {
+      uint4 u;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[k + 0], v[k + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(v[k + 2], v[k + 3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[k + 4], v[k + 5]);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(v[k + 6], v[k + 7]);
+      u.x = *reinterpret_cast<uint32_t*>(&h0);
+      u.y = *reinterpret_cast<uint32_t*>(&h1);
+      u.z = *reinterpret_cast<uint32_t*>(&h2);
+      u.w = *reinterpret_cast<uint32_t*>(&h3);
+      *reinterpret_cast<uint4*>(p + k) = u;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+      uint2 u;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[k + 0], v[k + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(v[k + 2], v[k + 3]);
+      u.x = *reinterpret_cast<uint32_t*>(&h0);
+      u.y = *reinterpret_cast<uint32_t*>(&h1);
+      *reinterpret_cast<uint2*>(p + k) = u;
+    }
+  }
+}
+
+// Sum over the lanes of an aligned power-of-two segment of width W.
+template <int W>
+__device__ __forceinline__ float seg_sum(float v, unsigned mask) {
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+  return v;
+}
+template <int W>
+__device__ __forceinline__ float seg_max(float v, unsigned mask) {
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, off));
+  return v;
+}
+template <int W>
+__device__ __forceinline__ float seg_min(float v, unsigned mask) {
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, off));
+  return v;
+}
+template <int W>
+__device__ __forceinline__ uint32_t seg_or(uint32_t v, unsigned mask) {
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(mask, v, off);
+  return v;
+}
+
+template <int LPR>
+__device__ __forceinline__ unsigned segment_mask(int lane) {
+  if constexpr (LPR == 32) {
+    return 0xffffffffu;
+  } else {
+    return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
+  }
+}
+
+}  // namespace cpra

@@ -1,0 +1,1075 @@
+// C-ABI of the CPRA step: context management, graph validation and upload,
+// workspace layout in HBM, and the per-step kernel schedule.
+//
+// Step schedule (one CUDA stream, no host synchronisation unless asked):
+//   forward   SPMM  M1 = mean_agg(X0)              -> XM[:, H0:]
+//             GEMM  H1 = relu([X0|M1] Wcat1^T + b1)  -> HM[:, :H1]
+//             SPMM  M2 = mean_agg(H1)              -> HM[:, H1:]
+//             GEMM  P  = sigmoid([H1|M2] Wcat2^T + b2)
+//   loss      fused SpMM + loss + rounding/eval     -> G_Z2, per-shot terms, x bits, counts
+//   adjoint   GEMM  [G_H1a | G_M2/deg] = G_Z2 Wcat2
+//             SPMM  G_Z1 = (G_H1a + A G_M2/deg) * 1[H1 > 0]   (+ db1 column sums)
+//             GEMM  dWcat2 = G_Z2^T [H1|M2],  dWcat1 = G_Z1^T [X0|M1]   (split-K)
+//             GEMM  [G_X0a | G_M1/deg] = G_Z1 Wcat1;  SPMM dX0 = G_X0a + A G_M1/deg
+//   update    Adam on theta (+ BF16 weight shadows), Adam on the embeddings
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cpra.h"
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+using namespace cpra;
+
+namespace {
+
+enum KernelId {
+  K_SPMM_AGG1 = 0,
+  K_GEMM_L1,
+  K_SPMM_AGG2,
+  K_GEMM_L2,
+  K_LOSS,
+  K_LOSS_FIN,
+  K_GEMM_DGRAD2,
+  K_SPMM_BWD2,
+  K_WGRAD2,
+  K_WGRAD1,
+  K_GEMM_DGRAD1,
+  K_SPMM_BWD1,
+  K_ADAM,
+  K_ADAM_EMB,
+  K_COUNT_
+};
+
+const char* kKernelNames[K_COUNT_] = {
+    "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
+    "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
+    "gemm_dgrad1", "spmm_bwd1",   "adam",       "adam_embedding"};
+
+constexpr size_t kAlign = 256;
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return n > 0 ? n : 148;
+}
+
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+
+// Message of the last failed cpra_init_graph on this thread.
+thread_local std::string g_init_err;
+
+}  // namespace
+
+struct cpra_ctx {
+  cpra_config cfg{};
+  std::vector<float> lambda_h;
+  int64_t N = 0, nnz = 0, nparam = 0;
+  int S = 0, S_pad = 0, W = 0, H0 = 0, H1 = 0, act_dt = DT_F32;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  float* inv_deg = nullptr;
+  float* lambda_d = nullptr;
+  float* theta = nullptr;
+  float* theta_m = nullptr;
+  float* theta_v = nullptr;
+  float* grad = nullptr;
+  float* X0m = nullptr;
+  float* X0_m = nullptr;
+  float* X0_v = nullptr;
+  float* gX0 = nullptr;
+  void* XM = nullptr;
+  void* HM = nullptr;
+  float* P = nullptr;
+  void* GZ2 = nullptr;
+  void* GHM = nullptr;
+  void* GXM = nullptr;
+  uint32_t* xbits = nullptr;
+  float* loss_part = nullptr;
+  int64_t pstride = 0;
+  float* terms = nullptr;
+  unsigned long long* counters = nullptr;
+  void* eval_rec = nullptr;
+  long long* ham_d = nullptr;
+  float* colsum_part = nullptr;
+  float* wg_part = nullptr;
+  size_t wg_part_floats = 0;
+  int* err_flag = nullptr;
+  void* W1s = nullptr;
+  void* W1t = nullptr;
+  void* W2s = nullptr;
+  void* W2t = nullptr;
+
+  int64_t opt_steps = 0;
+  int64_t launches = 0;
+  bool have_eval = false;
+  bool use_tc = false;
+  std::string err;
+
+  bool prof = false;
+  std::vector<ProfRec> prof_ring;
+  size_t prof_used = 0;
+  double prof_ms[K_COUNT_] = {0};
+  int64_t prof_n[K_COUNT_] = {0};
+  std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace {
+
+cpra_status fail(cpra_ctx* c, cpra_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+cpra_status cuda_check(cpra_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CPRA_OK;
+  return fail(c, CPRA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Offsets into the flat theta vector.
+struct Layout {
+  int64_t wcat1, b1, wcat2, b2, total;
+};
+Layout layout_of(int H0, int H1, int S) {
+  Layout L;
+  L.wcat1 = 0;
+  L.b1 = (int64_t)H1 * 2 * H0;
+  L.wcat2 = L.b1 + H1;
+  L.b2 = L.wcat2 + (int64_t)S * 2 * H1;
+  L.total = L.b2 + S;
+  return L;
+}
+
+std::string validate_config(const cpra_config* cfg) {
+  if (!cfg) return "cfg is NULL";
+  if (cfg->problem != CPRA_MIS && cfg->problem != CPRA_MAXCUT) return "problem must be MIS or MAXCUT";
+  if (cfg->S < 1 || cfg->S > 1024) return "S must be in [1, 1024]";
+  if (cfg->H0 < 16 || cfg->H0 > 1024 || cfg->H0 % 16) return "H0 must be a multiple of 16 in [16, 1024]";
+  if (cfg->H1 < 16 || cfg->H1 > 1024 || cfg->H1 % 16) return "H1 must be a multiple of 16 in [16, 1024]";
+  if (cfg->alpha < 2 || cfg->alpha > 32 || cfg->alpha % 2) return "alpha must be even, 2..32";
+  if (cfg->precision != CPRA_FP32 && cfg->precision != CPRA_BF16) return "precision must be FP32 or BF16";
+  if (cfg->diversity_kind != CPRA_DIV_STD && cfg->diversity_kind != CPRA_DIV_VAR) return "bad diversity_kind";
+  if (cfg->problem == CPRA_MIS && cfg->lambda == nullptr) return "MIS needs lambda[S]";
+  if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
+  if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+      !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps >= 0.f) || !(cfg->weight_decay >= 0.f))
+    return "bad optimiser hyper-parameters";
+  if (!std::isfinite(cfg->nu) || !std::isfinite(cfg->gamma0) || !std::isfinite(cfg->gamma1))
+    return "nu / gamma must be finite";
+  return "";
+}
+
+std::string validate_graph(int64_t N, const int64_t* rowptr, const int32_t* col) {
+  if (N < 1 || N > 0x7fffffffLL) return "N must be in [1, 2^31-1]";
+  if (!rowptr) return "rowptr is NULL";
+  if (rowptr[0] != 0) return "rowptr[0] must be 0";
+  for (int64_t i = 0; i < N; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return "rowptr must be non-decreasing";
+  const int64_t nnz = rowptr[N];
+  if (nnz >= 0x7fffffffLL) return "nnz must be < 2^31";
+  if (nnz > 0 && !col) return "col is NULL";
+  for (int64_t i = 0; i < N; ++i) {
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t j = col[e];
+      if (j < 0 || j >= N) return "column index out of range";
+      if (j == i) return "self-loop at node " + std::to_string(i);
+      if (e > rowptr[i] && col[e - 1] >= j) return "columns must be strictly increasing within a row";
+      // symmetry: i must appear in row j
+      const int32_t* b = col + rowptr[j];
+      const int32_t* en = col + rowptr[j + 1];
+      if (!std::binary_search(b, en, (int32_t)i))
+        return "graph is not symmetric: (" + std::to_string(i) + "," + std::to_string(j) + ")";
+    }
+  }
+  return "";
+}
+
+// Carves every device buffer; with base == nullptr only sizes the layout.
+size_t carve(cpra_ctx* c, void* base) {
+  Carver cv(base);
+  const int64_t N = c->N;
+  const size_t act = c->act_dt == DT_BF16 ? 2 : 4;
+  c->rowptr = cv.take<int>(N + 1);
+  c->col = cv.take<int>(std::max<int64_t>(c->nnz, 1));
+  c->inv_deg = cv.take<float>(N);
+  c->lambda_d = cv.take<float>(c->S);
+  c->theta = cv.take<float>(c->nparam);
+  c->theta_m = cv.take<float>(c->nparam);
+  c->theta_v = cv.take<float>(c->nparam);
+  c->grad = cv.take<float>(c->nparam);
+  c->X0m = cv.take<float>(N * c->H0);
+  c->X0_m = cv.take<float>(N * c->H0);
+  c->X0_v = cv.take<float>(N * c->H0);
+  c->gX0 = cv.take<float>(N * c->H0);
+  c->XM = cv.take<char>((size_t)N * 2 * c->H0 * act);
+  c->HM = cv.take<char>((size_t)N * 2 * c->H1 * act);
+  c->P = cv.take<float>((size_t)N * c->S_pad);
+  c->GZ2 = cv.take<char>((size_t)N * c->S_pad * act);
+  c->GHM = cv.take<char>((size_t)N * 2 * c->H1 * act);
+  c->GXM = cv.take<char>((size_t)N * 2 * c->H0 * act);
+  c->xbits = cv.take<uint32_t>((size_t)N * c->W);
+  c->pstride = loss_pstride(c->S);
+  c->loss_part = cv.take<float>((size_t)kLossMaxGrid * c->pstride);
+  c->terms = cv.take<float>(4 * (size_t)c->S + 1);
+  c->counters = cv.take<unsigned long long>(2 * (size_t)c->S + 1);
+  c->eval_rec = cv.take<cpra_shot_eval>(c->S);
+  c->ham_d = cv.take<long long>(1);
+  c->colsum_part = cv.take<float>((size_t)kLossMaxGrid * c->H1);
+  // split-K partials: up to 4*num_sms slabs of the larger weight gradient
+  const size_t slab = std::max((size_t)c->S_pad * 2 * c->H1, (size_t)c->H1 * 2 * c->H0);
+  c->wg_part_floats = slab * (size_t)(4 * c->num_sms);
+  c->wg_part = cv.take<float>(c->wg_part_floats);
+  c->err_flag = cv.take<int>(4);
+  c->W1s = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
+  c->W1t = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
+  c->W2s = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
+  c->W2t = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
+  return cv.off + kAlign;
+}
+
+void set_dims(cpra_ctx* c, int64_t N, int64_t nnz, const cpra_config* cfg) {
+  c->N = N;
+  c->nnz = nnz;
+  c->S = cfg->S;
+  c->S_pad = round_up(cfg->S, 16);
+  c->W = (cfg->S + 31) / 32;
+  c->H0 = cfg->H0;
+  c->H1 = cfg->H1;
+  c->act_dt = cfg->precision == CPRA_BF16 ? DT_BF16 : DT_F32;
+  c->nparam = layout_of(cfg->H0, cfg->H1, cfg->S).total;
+}
+
+// ---------------------------------------------------------------- profiling
+struct Region {
+  cpra_ctx* c;
+  int id;
+  size_t slot = (size_t)-1;
+  Region(cpra_ctx* ctx, int kid) : c(ctx), id(kid) {
+    if (!c->prof) return;
+    if (c->prof_used == c->prof_ring.size()) {
+      // flush: synchronise and accumulate
+      cudaStreamSynchronize(c->stream);
+      for (size_t k = 0; k < c->prof_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ring[k].a, c->prof_ring[k].b) == cudaSuccess) {
+          c->prof_ms[c->prof_ring[k].id] += ms;
+          c->prof_n[c->prof_ring[k].id] += 1;
+        }
+      }
+      c->prof_used = 0;
+    }
+    slot = c->prof_used++;
+    c->prof_ring[slot].id = id;
+    cudaEventRecord(c->prof_ring[slot].a, c->stream);
+  }
+  ~Region() {
+    if (slot != (size_t)-1) cudaEventRecord(c->prof_ring[slot].b, c->stream);
+  }
+};
+
+void refresh_shadows(cpra_ctx* c) {
+  if (c->act_dt == DT_BF16) {
+    weight_shadows_launch(c->theta, c->H0, c->H1, c->S, c->S_pad, c->W1s, c->W1t, c->W2s,
+                          c->W2t, c->stream);
+    c->launches += 1;
+  }
+}
+
+void refresh_emb_shadow(cpra_ctx* c) {
+  copy_rows_launch(c->N, c->H0, c->X0m, c->XM, 2 * c->H0, c->act_dt, c->stream);
+  c->launches += 1;
+}
+
+float gamma_at(const cpra_config& cfg, int64_t t) {
+  if (cfg.schedule_steps <= 1) return cfg.gamma1;
+  const int64_t tt = std::min<int64_t>(std::max<int64_t>(t, 0), cfg.schedule_steps - 1);
+  return (float)((double)cfg.gamma0 +
+                 ((double)cfg.gamma1 - (double)cfg.gamma0) * (double)tt /
+                     (double)(cfg.schedule_steps - 1));
+}
+
+size_t act_bytes(const cpra_ctx* c) { return c->act_dt == DT_BF16 ? 2 : 4; }
+char* act_off(void* base, int64_t elems, const cpra_ctx* c) {
+  return static_cast<char*>(base) + elems * (int64_t)act_bytes(c);
+}
+
+// Dense layer dispatch: tensor cores (BF16 form) or CUDA cores.
+void dense(cpra_ctx* c, const GemmArgs& g) {
+  if (c->use_tc && tc_gemm_supported(g)) {
+    c->launches += tc_gemm_launch(g, c->num_sms, c->stream);
+  } else {
+    gemm_simt_launch(g, c->stream);
+    c->launches += 1;
+  }
+}
+
+// Weight gradient C[M x Nc] = A^T B over K = N rows, split-K with a fixed-
+// order reduction into dst (row stride ldo).
+void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_t ldb, int Nc,
+           float* dst, int64_t ldo) {
+  GemmArgs g;
+  g.M = M;
+  g.Nc = Nc;
+  g.K = c->N;
+  g.A = A;
+  g.lda = lda;
+  g.da = c->act_dt;
+  g.a_kmajor = 0;
+  g.B = B;
+  g.ldb = ldb;
+  g.db = c->act_dt;
+  g.b_kmajor = 0;
+  g.epi = EPI_PARTIAL;
+  g.out0 = c->wg_part;
+  g.ld0 = Nc;
+  const int64_t tiles = ((int64_t)(M + 63) / 64) * ((Nc + 63) / 64);
+  int64_t splits = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + tiles - 1) / tiles);
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, c->N / 256));
+  const int64_t cap = (int64_t)(c->wg_part_floats / ((size_t)M * Nc));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, cap));
+  g.splits = (int)splits;
+  if (c->use_tc && tc_wgrad_supported(g)) {
+    c->launches += tc_wgrad_launch(g, c->num_sms, c->wg_part_floats, dst, ldo, c->stream);
+    return;
+  }
+  gemm_simt_launch(g, c->stream);
+  splitk_reduce(c->wg_part, g.splits, M, Nc, Nc, dst, ldo, c->stream);
+  c->launches += 2;
+}
+
+cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
+  const int64_t N = c->N;
+  const int H0 = c->H0, H1 = c->H1;
+  const int max_grid = c->num_sms * 8;
+  const Layout L = layout_of(H0, H1, c->S);
+  {  // M1 = mean_agg(X0)
+    Region r(c, K_SPMM_AGG1);
+    SpmmArgs a;
+    a.N = N; a.H = H0; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
+    a.X = c->XM; a.ldx = 2 * H0; a.Y = act_off(c->XM, H0, c); a.ldy = 2 * H0; a.mean = 1;
+    a.dx = c->act_dt; a.dy = c->act_dt;
+    spmm_launch(a, max_grid, c->stream);
+    c->launches += 1;
+  }
+  {  // H1 = relu([X0|M1] Wcat1^T + b1)
+    Region r(c, K_GEMM_L1);
+    GemmArgs g;
+    g.M = N; g.Nc = H1; g.K = 2 * H0;
+    g.A = c->XM; g.lda = 2 * H0; g.da = c->act_dt; g.a_kmajor = 1;
+    if (c->act_dt == DT_BF16) { g.B = c->W1s; g.db = DT_BF16; }
+    else { g.B = c->theta + L.wcat1; g.db = DT_F32; }
+    g.ldb = 2 * H0; g.b_kmajor = 1;
+    g.epi = EPI_BIAS_RELU; g.bias = c->theta + L.b1;
+    g.out0 = c->HM; g.ld0 = 2 * H1; g.d0 = c->act_dt; g.n_valid = H1;
+    dense(c, g);
+  }
+  {  // M2 = mean_agg(H1)
+    Region r(c, K_SPMM_AGG2);
+    SpmmArgs a;
+    a.N = N; a.H = H1; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
+    a.X = c->HM; a.ldx = 2 * H1; a.Y = act_off(c->HM, H1, c); a.ldy = 2 * H1; a.mean = 1;
+    a.dx = c->act_dt; a.dy = c->act_dt;
+    spmm_launch(a, max_grid, c->stream);
+    c->launches += 1;
+  }
+  {  // P = sigmoid([H1|M2] Wcat2^T + b2)
+    Region r(c, K_GEMM_L2);
+    GemmArgs g;
+    g.M = N; g.Nc = c->S_pad; g.K = 2 * H1;
+    g.A = c->HM; g.lda = 2 * H1; g.da = c->act_dt; g.a_kmajor = 1;
+    if (c->act_dt == DT_BF16) { g.B = c->W2s; g.db = DT_BF16; }
+    else { g.B = c->theta + L.wcat2; g.db = DT_F32; }
+    g.ldb = 2 * H1; g.b_kmajor = 1;
+    g.epi = EPI_BIAS_SIGMOID; g.bias = c->theta + L.b2;
+    g.out0 = c->P; g.ld0 = c->S_pad; g.d0 = DT_F32; g.n_valid = c->S;
+    dense(c, g);
+  }
+  {  // fused SpMM + loss + rounding / integer evaluation
+    Region r(c, K_LOSS);
+    cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
+                    c->stream);
+    LossArgs a;
+    a.N = N; a.S = c->S; a.ldp = c->S_pad; a.ldg = c->S_pad;
+    a.rowptr = c->rowptr; a.col = c->col; a.P = c->P; a.lambda = c->lambda_d;
+    a.problem = c->cfg.problem; a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
+    a.grad_kind = 0; a.gamma = gamma; a.nu = c->cfg.nu;
+    a.G = c->GZ2; a.dg = c->act_dt; a.xbits = c->xbits;
+    a.partials = c->loss_part; a.pstride = c->pstride; a.counters = c->counters;
+    a.do_loss = do_loss ? 1 : 0;
+    const int grid = loss_launch(a, c->num_sms * 4, c->stream);
+    c->launches += 1;
+    Region r2(c, K_LOSS_FIN);
+    if (do_loss) {
+      colsum_finalize(c->loss_part, grid, c->pstride, 4 * c->S + 1, c->terms, c->grad + L.b2,
+                      3 * c->S + 1, c->S, c->err_flag, c->stream);
+      c->launches += 1;
+    }
+    eval_finalize(c->counters, c->S, c->cfg.problem, c->lambda_d, c->eval_rec, c->ham_d,
+                  c->stream);
+    c->launches += 1;
+  }
+  c->have_eval = true;
+  return CPRA_OK;
+}
+
+cpra_status run_backward_and_update(cpra_ctx* c) {
+  const int64_t N = c->N;
+  const int H0 = c->H0, H1 = c->H1;
+  const int max_grid = c->num_sms * 8;
+  const Layout L = layout_of(H0, H1, c->S);
+  const bool bf = c->act_dt == DT_BF16;
+  {  // [G_H1a | G_M2/deg] = G_Z2 Wcat2
+    Region r(c, K_GEMM_DGRAD2);
+    GemmArgs g;
+    g.M = N; g.Nc = 2 * H1;
+    g.A = c->GZ2; g.lda = c->S_pad; g.da = c->act_dt; g.a_kmajor = 1;
+    if (bf) { g.K = c->S_pad; g.B = c->W2t; g.ldb = c->S_pad; g.db = DT_BF16; g.b_kmajor = 1; }
+    else { g.K = c->S; g.B = c->theta + L.wcat2; g.ldb = 2 * H1; g.db = DT_F32; g.b_kmajor = 0; }
+    g.epi = EPI_SPLIT; g.split = H1;
+    g.out0 = c->GHM; g.ld0 = 2 * H1; g.d0 = c->act_dt;
+    g.out1 = act_off(c->GHM, H1, c); g.ld1 = 2 * H1; g.d1 = c->act_dt;
+    g.row_scale = c->inv_deg; g.n_valid = 2 * H1;
+    dense(c, g);
+  }
+  {  // G_Z1 = (G_H1a + sum_j G_M2_j/deg_j) * 1[H1 > 0], db1 = colsum(G_Z1)
+    Region r(c, K_SPMM_BWD2);
+    SpmmArgs a;
+    a.N = N; a.H = H1; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
+    a.X = act_off(c->GHM, H1, c); a.ldx = 2 * H1;
+    a.add = c->GHM; a.ldadd = 2 * H1;
+    a.mask = c->HM; a.ldm = 2 * H1;
+    a.Y = c->GHM; a.ldy = 2 * H1; a.mean = 0;
+    a.dx = c->act_dt; a.dy = c->act_dt;
+    a.colsum_partials = c->colsum_part;
+    const int grid = spmm_launch(a, std::min(max_grid, kLossMaxGrid), c->stream);
+    colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
+                    c->stream);
+    c->launches += 2;
+  }
+  {
+    Region r(c, K_WGRAD2);  // dWcat2 = G_Z2^T [H1|M2]
+    wgrad(c, c->GZ2, c->S_pad, c->S, c->HM, 2 * H1, 2 * H1, c->grad + L.wcat2, 2 * H1);
+  }
+  {
+    Region r(c, K_WGRAD1);  // dWcat1 = G_Z1^T [X0|M1]
+    wgrad(c, c->GHM, 2 * H1, H1, c->XM, 2 * H0, 2 * H0, c->grad + L.wcat1, 2 * H0);
+  }
+  if (c->cfg.train_embedding) {
+    {  // [G_X0a | G_M1/deg] = G_Z1 Wcat1
+      Region r(c, K_GEMM_DGRAD1);
+      GemmArgs g;
+      g.M = N; g.Nc = 2 * H0; g.K = H1;
+      g.A = c->GHM; g.lda = 2 * H1; g.da = c->act_dt; g.a_kmajor = 1;
+      if (bf) { g.B = c->W1t; g.ldb = H1; g.db = DT_BF16; g.b_kmajor = 1; }
+      else { g.B = c->theta + L.wcat1; g.ldb = 2 * H0; g.db = DT_F32; g.b_kmajor = 0; }
+      g.epi = EPI_SPLIT; g.split = H0;
+      g.out0 = c->GXM; g.ld0 = 2 * H0; g.d0 = c->act_dt;
+      g.out1 = act_off(c->GXM, H0, c); g.ld1 = 2 * H0; g.d1 = c->act_dt;
+      g.row_scale = c->inv_deg; g.n_valid = 2 * H0;
+      dense(c, g);
+    }
+    {  // dX0 = G_X0a + sum_j G_M1_j/deg_j
+      Region r(c, K_SPMM_BWD1);
+      SpmmArgs a;
+      a.N = N; a.H = H0; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
+      a.X = act_off(c->GXM, H0, c); a.ldx = 2 * H0;
+      a.add = c->GXM; a.ldadd = 2 * H0;
+      a.Y = c->gX0; a.ldy = H0; a.mean = 0;
+      a.dx = c->act_dt; a.dy = DT_F32;
+      spmm_launch(a, max_grid, c->stream);
+      c->launches += 1;
+    }
+  }
+  const int64_t t = c->opt_steps + 1;
+  const float bc1 = (float)(1.0 - std::pow((double)c->cfg.beta1, (double)t));
+  const float bc2 = (float)(1.0 - std::pow((double)c->cfg.beta2, (double)t));
+  {
+    Region r(c, K_ADAM);
+    adam_launch(c->nparam, c->theta, c->theta_m, c->theta_v, c->grad, c->cfg.lr, c->cfg.beta1,
+                c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, c->stream);
+    c->launches += 1;
+    refresh_shadows(c);
+  }
+  if (c->cfg.train_embedding) {
+    Region r(c, K_ADAM_EMB);
+    adam_emb_launch(N, H0, c->X0m, c->X0_m, c->X0_v, c->gX0, c->cfg.lr, c->cfg.beta1,
+                    c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, c->XM, 2 * H0,
+                    c->act_dt, c->stream);
+    c->launches += 1;
+  }
+  c->opt_steps += 1;
+  return CPRA_OK;
+}
+
+cpra_status check_err_flag(cpra_ctx* c) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "error-flag readback");
+  if (flag & 2) {
+    cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream);
+    return fail(c, CPRA_ETIMEOUT, "a bounded device-side wait gave up (tensor-core pipeline)");
+  }
+  if (flag & 1) {
+    cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream);
+    return fail(c, CPRA_ENUMERIC, "non-finite loss term");
+  }
+  return CPRA_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void cpra_config_default(cpra_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->problem = CPRA_MIS;
+  cfg->S = 8;
+  cfg->H0 = 16;
+  cfg->H1 = 16;
+  cfg->alpha = 2;
+  cfg->precision = CPRA_FP32;
+  cfg->recompute = 0;
+  cfg->train_embedding = 1;
+  cfg->diversity_kind = CPRA_DIV_STD;
+  cfg->lambda = nullptr;
+  cfg->nu = 0.f;
+  cfg->gamma0 = -2.f;
+  cfg->gamma1 = 0.1f;
+  cfg->schedule_steps = 3000;
+  cfg->lr = 1e-3f;
+  cfg->beta1 = 0.9f;
+  cfg->beta2 = 0.999f;
+  cfg->eps = 1e-8f;
+  cfg->weight_decay = 0.f;
+  cfg->seed = 1;
+  cfg->mem_cap_bytes = 0;
+}
+
+int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S) {
+  return 2 * (int64_t)H1 * H0 + H1 + 2 * (int64_t)S * H1 + S;
+}
+
+size_t cpra_workspace_bytes(int64_t N, int64_t nnz, const cpra_config* cfg) {
+  if (!validate_config(cfg).empty() || N < 1 || nnz < 0) return 0;
+  cpra_ctx tmp;
+  tmp.num_sms = device_sm_count();
+  set_dims(&tmp, N, nnz, cfg);
+  return carve(&tmp, nullptr);
+}
+
+cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
+                            const int32_t* col, const float* w, const cpra_config* cfg,
+                            void* dev_workspace, size_t workspace_bytes, void* cuda_stream) {
+  if (!out) return CPRA_EINVAL;
+  *out = nullptr;
+  cpra_ctx* c = new (std::nothrow) cpra_ctx();
+  if (!c) return CPRA_ENOMEM;
+  auto bail = [&](cpra_status s) {
+    g_init_err = c->err;
+    cpra_destroy(c);
+    return s;
+  };
+  std::string msg = validate_config(cfg);
+  if (!msg.empty()) { fail(c, CPRA_EINVAL, msg); return bail(CPRA_EINVAL); }
+  if (w != nullptr) { fail(c, CPRA_EINVAL, "edge weights are not supported (w must be NULL)"); return bail(CPRA_EINVAL); }
+  msg = validate_graph(N, rowptr, col);
+  if (!msg.empty()) { fail(c, CPRA_EINVAL, msg); return bail(CPRA_EINVAL); }
+  c->cfg = *cfg;
+  c->num_sms = device_sm_count();
+  set_dims(c, N, rowptr[N], cfg);
+  c->lambda_h.assign((size_t)c->S, 0.f);
+  if (cfg->lambda) std::memcpy(c->lambda_h.data(), cfg->lambda, sizeof(float) * c->S);
+  c->cfg.lambda = nullptr;
+  c->use_tc = (c->act_dt == DT_BF16) && tc_available();
+
+  const size_t need = carve(c, nullptr);
+  if (cfg->mem_cap_bytes && need > cfg->mem_cap_bytes) {
+    fail(c, CPRA_ENOMEM, "workspace of " + std::to_string(need) + " bytes exceeds mem_cap_bytes");
+    return bail(CPRA_ENOMEM);
+  }
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cuda_check(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream") != CPRA_OK)
+      return bail(CPRA_ECUDA);
+    c->own_stream = true;
+  }
+  if (dev_workspace) {
+    if (workspace_bytes < need) {
+      fail(c, CPRA_EINVAL, "workspace too small: need " + std::to_string(need));
+      return bail(CPRA_EINVAL);
+    }
+    c->ws = dev_workspace;
+    c->ws_bytes = workspace_bytes;
+  } else {
+    cudaError_t e = cudaMalloc(&c->ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, CPRA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return bail(CPRA_ENOMEM);
+    }
+    c->own_ws = true;
+    c->ws_bytes = need;
+  }
+  // align the carve base
+  char* base = reinterpret_cast<char*>(
+      (reinterpret_cast<uintptr_t>(c->ws) + kAlign - 1) / kAlign * kAlign);
+  carve(c, base);
+
+  // graph upload (int32 row pointers, inverse degrees)
+  std::vector<int> rp32((size_t)N + 1);
+  std::vector<float> invd((size_t)N);
+  for (int64_t i = 0; i <= N; ++i) rp32[i] = (int)rowptr[i];
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t d = rowptr[i + 1] - rowptr[i];
+    invd[i] = d > 0 ? (float)(1.0 / (double)d) : 0.f;
+  }
+  cudaStream_t st = c->stream;
+  cpra_status s = CPRA_OK;
+  s = cuda_check(c, cudaMemcpyAsync(c->rowptr, rp32.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st), "upload rowptr");
+  if (s == CPRA_OK && c->nnz > 0)
+    s = cuda_check(c, cudaMemcpyAsync(c->col, col, sizeof(int) * c->nnz, cudaMemcpyHostToDevice, st), "upload col");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpyAsync(c->inv_deg, invd.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st), "upload inv_deg");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpyAsync(c->lambda_d, c->lambda_h.data(), sizeof(float) * c->S, cudaMemcpyHostToDevice, st), "upload lambda");
+  if (s != CPRA_OK) return bail(s);
+  // zero everything that must start at zero (pads included)
+  const size_t act = act_bytes(c);
+  cudaMemsetAsync(c->theta_m, 0, sizeof(float) * c->nparam, st);
+  cudaMemsetAsync(c->theta_v, 0, sizeof(float) * c->nparam, st);
+  cudaMemsetAsync(c->grad, 0, sizeof(float) * c->nparam, st);
+  cudaMemsetAsync(c->X0_m, 0, sizeof(float) * N * c->H0, st);
+  cudaMemsetAsync(c->X0_v, 0, sizeof(float) * N * c->H0, st);
+  cudaMemsetAsync(c->gX0, 0, sizeof(float) * N * c->H0, st);
+  cudaMemsetAsync(c->P, 0, sizeof(float) * N * c->S_pad, st);
+  cudaMemsetAsync(c->GZ2, 0, act * N * c->S_pad, st);
+  cudaMemsetAsync(c->err_flag, 0, sizeof(int) * 4, st);
+  cudaMemsetAsync(c->terms, 0, sizeof(float) * (4 * c->S + 1), st);
+  // parameters: U(+-1/sqrt(fan_in)) for weights and biases, N(0,1) embeddings
+  const Layout L = layout_of(c->H0, c->H1, c->S);
+  const uint64_t seed = cfg->seed;
+  init_uniform_launch(c->theta + L.wcat1, L.b1 - L.wcat1, 1.f / std::sqrt((float)c->H0), seed, 1, st);
+  init_uniform_launch(c->theta + L.b1, c->H1, 1.f / std::sqrt((float)c->H0), seed, 2, st);
+  init_uniform_launch(c->theta + L.wcat2, L.b2 - L.wcat2, 1.f / std::sqrt((float)c->H1), seed, 3, st);
+  init_uniform_launch(c->theta + L.b2, c->S, 1.f / std::sqrt((float)c->H1), seed, 4, st);
+  init_normal_launch(c->X0m, N * c->H0, seed, 5, st);
+  c->launches += 5;
+  refresh_shadows(c);
+  refresh_emb_shadow(c);
+  if (c->use_tc) {
+    std::string tmsg;
+    if (!tc_prepare(c->num_sms, &tmsg)) {
+      c->use_tc = false;
+    }
+  }
+  s = cuda_check(c, cudaStreamSynchronize(st), "init");
+  if (s == CPRA_OK) s = cuda_check(c, cudaGetLastError(), "init kernels");
+  if (s != CPRA_OK) return bail(s);
+  *out = c;
+  return CPRA_OK;
+}
+
+cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
+  if (!c) return CPRA_EINVAL;
+  const float gamma = gamma_at(c->cfg, t);
+  cpra_status s = run_forward_and_loss(c, gamma, true);
+  if (s != CPRA_OK) return s;
+  s = run_backward_and_update(c);
+  if (s != CPRA_OK) return s;
+  s = cuda_check(c, cudaGetLastError(), "step kernels");
+  if (s != CPRA_OK) return s;
+  if (loss_terms_out) {
+    s = cuda_check(c, cudaMemcpyAsync(loss_terms_out, c->terms, sizeof(float) * (3 * c->S + 1),
+                                      cudaMemcpyDeviceToHost, c->stream), "terms readback");
+    if (s != CPRA_OK) return s;
+    s = check_err_flag(c);
+    if (s != CPRA_OK) return s;
+  }
+  return CPRA_OK;
+}
+
+cpra_status cpra_round_eval(cpra_ctx* c, cpra_shot_eval* out, int64_t* pair_hamming_sum,
+                            uint32_t* x_bits_out) {
+  if (!c || !out) return c ? fail(c, CPRA_EINVAL, "out is NULL") : CPRA_EINVAL;
+  if (!c->have_eval) {
+    cpra_status s = run_forward_and_loss(c, gamma_at(c->cfg, 0), false);
+    if (s != CPRA_OK) return s;
+  }
+  cudaStream_t st = c->stream;
+  cpra_status s = cuda_check(c, cudaMemcpyAsync(out, c->eval_rec, sizeof(cpra_shot_eval) * c->S,
+                                                cudaMemcpyDeviceToHost, st), "eval readback");
+  if (s == CPRA_OK && pair_hamming_sum)
+    s = cuda_check(c, cudaMemcpyAsync(pair_hamming_sum, c->ham_d, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, st), "hamming readback");
+  if (s == CPRA_OK && x_bits_out)
+    s = cuda_check(c, cudaMemcpyAsync(x_bits_out, c->xbits, sizeof(uint32_t) * c->N * c->W,
+                                      cudaMemcpyDeviceToHost, st), "bits readback");
+  if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "eval sync");
+  return s;
+}
+
+cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot_eval* best_out,
+                       int64_t* best_step_out) {
+  if (!c || !best_out || steps < 1) return c ? fail(c, CPRA_EINVAL, "bad solve arguments") : CPRA_EINVAL;
+  if (eval_every < 1) eval_every = steps;
+  std::vector<cpra_shot_eval> cur((size_t)c->S);
+  std::vector<int64_t> best_step((size_t)c->S, -1);
+  for (int s = 0; s < c->S; ++s) {
+    best_out[s].objective = -1;
+    best_out[s].violations = 0;
+    best_out[s].qubo = 0.0;
+  }
+  for (int64_t t = 0; t < steps; ++t) {
+    cpra_status st = cpra_step(c, t, nullptr);
+    if (st != CPRA_OK) return st;
+    if (t % eval_every == 0 || t == steps - 1) {
+      st = cpra_round_eval(c, cur.data(), nullptr, nullptr);
+      if (st != CPRA_OK) return st;
+      st = check_err_flag(c);
+      if (st != CPRA_OK) return st;
+      for (int s = 0; s < c->S; ++s) {
+        const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
+        if (ok && cur[s].objective > best_out[s].objective) {
+          best_out[s] = cur[s];
+          best_step[s] = t;
+        }
+      }
+    }
+  }
+  if (best_step_out) std::memcpy(best_step_out, best_step.data(), sizeof(int64_t) * c->S);
+  return CPRA_OK;
+}
+
+size_t cpra_tensor_bytes(const cpra_ctx* c, int32_t which) {
+  if (!c) return 0;
+  const size_t NH = (size_t)c->N * c->H0 * sizeof(float);
+  switch (which) {
+    case CPRA_T_THETA: case CPRA_T_THETA_M: case CPRA_T_THETA_V: case CPRA_T_GRAD:
+      return (size_t)c->nparam * sizeof(float);
+    case CPRA_T_EMB: case CPRA_T_EMB_M: case CPRA_T_EMB_V: case CPRA_T_EMB_GRAD:
+      return NH;
+    case CPRA_T_P: case CPRA_T_GZ2:
+      return (size_t)c->N * c->S * sizeof(float);
+    case CPRA_T_STEP:
+      return sizeof(int64_t);
+    case CPRA_T_TERMS:
+      return (3 * (size_t)c->S + 1) * sizeof(float);
+    default:
+      return 0;
+  }
+}
+
+static float* flat_ptr(cpra_ctx* c, int32_t which) {
+  switch (which) {
+    case CPRA_T_THETA: return c->theta;
+    case CPRA_T_THETA_M: return c->theta_m;
+    case CPRA_T_THETA_V: return c->theta_v;
+    case CPRA_T_GRAD: return c->grad;
+    case CPRA_T_EMB: return c->X0m;
+    case CPRA_T_EMB_M: return c->X0_m;
+    case CPRA_T_EMB_V: return c->X0_v;
+    case CPRA_T_EMB_GRAD: return c->gX0;
+    case CPRA_T_TERMS: return c->terms;
+    default: return nullptr;
+  }
+}
+
+static float bf16_bits_to_float(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+cpra_status cpra_get_tensor(cpra_ctx* c, int32_t which, void* host, size_t nbytes) {
+  if (!c || !host) return c ? fail(c, CPRA_EINVAL, "host is NULL") : CPRA_EINVAL;
+  const size_t want = cpra_tensor_bytes(c, which);
+  if (want == 0 || nbytes != want) return fail(c, CPRA_EINVAL, "bad tensor id or size");
+  cudaStream_t st = c->stream;
+  cpra_status s = CPRA_OK;
+  if (which == CPRA_T_STEP) {
+    s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+    std::memcpy(host, &c->opt_steps, sizeof(int64_t));
+    return s;
+  }
+  if (which == CPRA_T_P) {
+    s = cuda_check(c, cudaMemcpy2DAsync(host, sizeof(float) * c->S, c->P, sizeof(float) * c->S_pad,
+                                        sizeof(float) * c->S, c->N, cudaMemcpyDeviceToHost, st), "P");
+  } else if (which == CPRA_T_GZ2) {
+    if (c->act_dt == DT_F32) {
+      s = cuda_check(c, cudaMemcpy2DAsync(host, sizeof(float) * c->S, c->GZ2, sizeof(float) * c->S_pad,
+                                          sizeof(float) * c->S, c->N, cudaMemcpyDeviceToHost, st), "GZ2");
+    } else {
+      std::vector<uint16_t> tmp((size_t)c->N * c->S);
+      s = cuda_check(c, cudaMemcpy2DAsync(tmp.data(), 2 * c->S, c->GZ2, 2 * (size_t)c->S_pad, 2 * c->S,
+                                          c->N, cudaMemcpyDeviceToHost, st), "GZ2");
+      if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+      float* h = static_cast<float*>(host);
+      for (size_t k = 0; k < tmp.size(); ++k) h[k] = bf16_bits_to_float(tmp[k]);
+      return s;
+    }
+  } else {
+    s = cuda_check(c, cudaMemcpyAsync(host, flat_ptr(c, which), nbytes, cudaMemcpyDeviceToHost, st), "get");
+  }
+  if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+  return s;
+}
+
+cpra_status cpra_set_tensor(cpra_ctx* c, int32_t which, const void* host, size_t nbytes) {
+  if (!c || !host) return c ? fail(c, CPRA_EINVAL, "host is NULL") : CPRA_EINVAL;
+  const size_t want = cpra_tensor_bytes(c, which);
+  if (want == 0 || nbytes != want) return fail(c, CPRA_EINVAL, "bad tensor id or size");
+  cudaStream_t st = c->stream;
+  if (which == CPRA_T_STEP) {
+    cpra_status s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+    int64_t v;
+    std::memcpy(&v, host, sizeof(v));
+    if (v < 0) return fail(c, CPRA_EINVAL, "step counter must be >= 0");
+    c->opt_steps = v;
+    return s;
+  }
+  if (which == CPRA_T_P || which == CPRA_T_GZ2 || which == CPRA_T_TERMS)
+    return fail(c, CPRA_EINVAL, "tensor is read-only");
+  cpra_status s = cuda_check(c, cudaMemcpyAsync(flat_ptr(c, which), host, nbytes,
+                                                cudaMemcpyHostToDevice, st), "set");
+  if (s != CPRA_OK) return s;
+  if (which == CPRA_T_THETA) refresh_shadows(c);
+  if (which == CPRA_T_EMB) refresh_emb_shadow(c);
+  c->have_eval = false;
+  return cuda_check(c, cudaStreamSynchronize(st), "sync");
+}
+
+struct StateHeader {
+  char magic[8];
+  int64_t version, N, H0, H1, S, nparam, opt_steps;
+};
+
+cpra_status cpra_get_state(cpra_ctx* c, void* buf, size_t* nbytes) {
+  if (!c || !nbytes) return CPRA_EINVAL;
+  const size_t tb = (size_t)c->nparam * sizeof(float);
+  const size_t eb = (size_t)c->N * c->H0 * sizeof(float);
+  const size_t total = sizeof(StateHeader) + 3 * tb + 3 * eb;
+  if (!buf) { *nbytes = total; return CPRA_OK; }
+  if (*nbytes < total) return fail(c, CPRA_EINVAL, "state buffer too small");
+  StateHeader h{};
+  std::memcpy(h.magic, "CPRAST01", 8);
+  h.version = 1; h.N = c->N; h.H0 = c->H0; h.H1 = c->H1; h.S = c->S; h.nparam = c->nparam;
+  cpra_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+  if (s != CPRA_OK) return s;
+  h.opt_steps = c->opt_steps;
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const int32_t ids[6] = {CPRA_T_THETA, CPRA_T_THETA_M, CPRA_T_THETA_V,
+                          CPRA_T_EMB, CPRA_T_EMB_M, CPRA_T_EMB_V};
+  for (int k = 0; k < 6; ++k) {
+    const size_t nb = k < 3 ? tb : eb;
+    s = cpra_get_tensor(c, ids[k], p, nb);
+    if (s != CPRA_OK) return s;
+    p += nb;
+  }
+  *nbytes = total;
+  return CPRA_OK;
+}
+
+cpra_status cpra_set_state(cpra_ctx* c, const void* buf, size_t nbytes) {
+  if (!c || !buf) return CPRA_EINVAL;
+  const size_t tb = (size_t)c->nparam * sizeof(float);
+  const size_t eb = (size_t)c->N * c->H0 * sizeof(float);
+  const size_t total = sizeof(StateHeader) + 3 * tb + 3 * eb;
+  if (nbytes != total) return fail(c, CPRA_ESTATE, "state blob has the wrong size");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, "CPRAST01", 8) != 0 || h.version != 1 || h.N != c->N ||
+      h.H0 != c->H0 || h.H1 != c->H1 || h.S != c->S || h.nparam != c->nparam)
+    return fail(c, CPRA_ESTATE, "state blob does not match this context");
+  const char* p = static_cast<const char*>(buf) + sizeof(h);
+  const int32_t ids[6] = {CPRA_T_THETA, CPRA_T_THETA_M, CPRA_T_THETA_V,
+                          CPRA_T_EMB, CPRA_T_EMB_M, CPRA_T_EMB_V};
+  for (int k = 0; k < 6; ++k) {
+    const size_t nb = k < 3 ? tb : eb;
+    cpra_status s = cpra_set_tensor(c, ids[k], p, nb);
+    if (s != CPRA_OK) return s;
+    p += nb;
+  }
+  c->opt_steps = h.opt_steps;
+  return CPRA_OK;
+}
+
+cpra_status cpra_get_P(cpra_ctx* c, float* host_NxS) {
+  if (!c) return CPRA_EINVAL;
+  return cpra_get_tensor(c, CPRA_T_P, host_NxS, cpra_tensor_bytes(c, CPRA_T_P));
+}
+
+int64_t cpra_param_count(const cpra_ctx* c) { return c ? c->nparam : 0; }
+int64_t cpra_launch_count(const cpra_ctx* c) { return c ? c->launches : 0; }
+
+void cpra_profile_enable(cpra_ctx* c, int on) {
+  if (!c) return;
+  if (on && c->prof_ring.empty()) {
+    c->prof_ring.resize(4096);
+    for (auto& r : c->prof_ring) {
+      cudaEventCreate(&r.a);
+      cudaEventCreate(&r.b);
+    }
+  }
+  c->prof = on != 0 && !c->prof_ring.empty();
+}
+
+int32_t cpra_profile_read(cpra_ctx* c, double* ms_out, int64_t* launches_out, int32_t n_ids) {
+  if (!c) return 0;
+  cudaStreamSynchronize(c->stream);
+  for (size_t k = 0; k < c->prof_used; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ring[k].a, c->prof_ring[k].b) == cudaSuccess) {
+      c->prof_ms[c->prof_ring[k].id] += ms;
+      c->prof_n[c->prof_ring[k].id] += 1;
+    }
+  }
+  c->prof_used = 0;
+  const int n = std::min<int>(n_ids, K_COUNT_);
+  for (int k = 0; k < n; ++k) {
+    if (ms_out) ms_out[k] = c->prof_ms[k];
+    if (launches_out) launches_out[k] = c->prof_n[k];
+  }
+  for (int k = 0; k < K_COUNT_; ++k) {
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  return K_COUNT_;
+}
+
+const char* cpra_kernel_name(int32_t id) {
+  if (id < 0 || id >= K_COUNT_) return "";
+  return kKernelNames[id];
+}
+
+const char* cpra_last_error(const cpra_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+const char* cpra_status_string(cpra_status s) {
+  switch (s) {
+    case CPRA_OK: return "ok";
+    case CPRA_EINVAL: return "invalid argument";
+    case CPRA_ENOMEM: return "out of device memory";
+    case CPRA_ECUDA: return "CUDA error";
+    case CPRA_ENUMERIC: return "non-finite value";
+    case CPRA_ETIMEOUT: return "device wait timed out";
+    case CPRA_ESTATE: return "state mismatch";
+  }
+  return "unknown status";
+}
+
+void cpra_destroy(cpra_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->prof_ring) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+// ------------------------------------------------------------ op level
+size_t cpra_op_loss_scratch_bytes(int64_t N, int32_t S) {
+  (void)N;
+  if (S < 1 || S > 1024) return 0;
+  return (size_t)kLossMaxGrid * loss_pstride(S) * sizeof(float) +
+         kAlign + (2 * (size_t)S + 1) * sizeof(unsigned long long);
+}
+
+cpra_status cpra_op_loss(int64_t N, int32_t S, const int32_t* rowptr, const int32_t* col,
+                         const float* P, int64_t ldp, const float* lambda, int32_t problem,
+                         int32_t alpha, float gamma, float nu, int32_t diversity_kind,
+                         int32_t grad_kind, float* G, int64_t ldg, uint32_t* x_bits,
+                         float* terms, void* scratch, size_t scratch_bytes, void* cuda_stream) {
+  if (N < 1 || S < 1 || S > 1024 || !rowptr || !col || !P || !G || !terms || !scratch)
+    return CPRA_EINVAL;
+  if (ldp < S || ldp % 4 || ldg < S || ldg % 4 || ldg > round_up(S, 16)) return CPRA_EINVAL;
+  if (problem != CPRA_MIS && problem != CPRA_MAXCUT) return CPRA_EINVAL;
+  if (problem == CPRA_MIS && !lambda) return CPRA_EINVAL;
+  if (alpha < 2 || alpha % 2 || diversity_kind < 0 || diversity_kind > 1) return CPRA_EINVAL;
+  if (grad_kind != 0 && grad_kind != 1) return CPRA_EINVAL;
+  if (scratch_bytes < cpra_op_loss_scratch_bytes(N, S)) return CPRA_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Carver cv(scratch);
+  LossArgs a;
+  a.N = N; a.S = S; a.ldp = ldp; a.ldg = ldg; a.rowptr = rowptr; a.col = col; a.P = P;
+  a.lambda = lambda; a.problem = problem; a.alpha = alpha; a.div_kind = diversity_kind;
+  a.grad_kind = grad_kind; a.gamma = gamma; a.nu = nu; a.G = G; a.dg = DT_F32;
+  a.xbits = x_bits; a.pstride = loss_pstride(S);
+  a.partials = cv.take<float>((size_t)kLossMaxGrid * a.pstride);
+  a.counters = cv.take<unsigned long long>(2 * (size_t)S + 1);
+  a.do_loss = 1;
+  if (cudaMemsetAsync(a.counters, 0, (2 * (size_t)S + 1) * sizeof(unsigned long long), st) != cudaSuccess)
+    return CPRA_ECUDA;
+  const int grid = loss_launch(a, device_sm_count() * 4, st);
+  colsum_finalize(a.partials, grid, a.pstride, 4 * S + 1, terms, nullptr, 0, 0, nullptr, st);
+  return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
+}
+
+size_t cpra_op_round_eval_scratch_bytes(int32_t S) {
+  if (S < 1 || S > 1024) return 0;
+  return (2 * (size_t)S + 1) * sizeof(unsigned long long);
+}
+
+cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr, const int32_t* col,
+                               const float* P, int64_t ldp, const float* lambda, int32_t problem,
+                               uint32_t* x_bits, cpra_shot_eval* out, int64_t* pair_hamming,
+                               void* counters, size_t counters_bytes, void* cuda_stream) {
+  if (N < 1 || S < 1 || S > 1024 || !rowptr || !col || !P || !x_bits || !out || !pair_hamming ||
+      !counters)
+    return CPRA_EINVAL;
+  if (ldp < S || ldp % 4) return CPRA_EINVAL;
+  if (problem != CPRA_MIS && problem != CPRA_MAXCUT) return CPRA_EINVAL;
+  if (problem == CPRA_MIS && !lambda) return CPRA_EINVAL;
+  if (counters_bytes < cpra_op_round_eval_scratch_bytes(S)) return CPRA_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  LossArgs a;
+  a.N = N; a.S = S; a.ldp = ldp; a.ldg = round_up(S, 4); a.rowptr = rowptr; a.col = col; a.P = P;
+  a.lambda = lambda; a.problem = problem; a.xbits = x_bits;
+  a.counters = static_cast<unsigned long long*>(counters);
+  a.do_loss = 0;
+  if (cudaMemsetAsync(a.counters, 0, cpra_op_round_eval_scratch_bytes(S), st) != cudaSuccess)
+    return CPRA_ECUDA;
+  loss_launch(a, device_sm_count() * 4, st);
+  eval_finalize(a.counters, S, problem, lambda, out, reinterpret_cast<long long*>(pair_hamming), st);
+  return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
+}
+
+}  // extern "C"

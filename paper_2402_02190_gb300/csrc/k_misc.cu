@@ -1,0 +1,193 @@
+// Optimiser, weight shadows, parameter initialisation and layout copies.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cpra {
+
+namespace {
+
+// Adam (Kingma & Ba) with optional decoupled weight decay (AdamW), the
+// optimiser of the Experiments section; bias corrections bc1 = 1 - beta1^t,
+// bc2 = 1 - beta2^t come from the host.
+__device__ __forceinline__ float adam_one(float th, float& m, float& v, float g, float lr,
+                                          float b1, float b2, float eps, float wd, float bc1,
+                                          float bc2) {
+  if (wd != 0.f) th = th * (1.f - lr * wd);
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  const float mhat = m / bc1;
+  const float vhat = v / bc2;
+  return th - lr * mhat / (sqrtf(vhat) + eps);
+}
+
+__global__ void adam_kernel(int64_t n, float* __restrict__ th, float* __restrict__ m,
+                            float* __restrict__ v, const float* __restrict__ g, float lr,
+                            float b1, float b2, float eps, float wd, float bc1, float bc2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float mi = m[i], vi = v[i];
+    th[i] = adam_one(th[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
+    m[i] = mi;
+    v[i] = vi;
+  }
+}
+
+template <typename TS>
+__global__ void adam_emb_kernel(int64_t N, int H0, float* __restrict__ X0,
+                                float* __restrict__ m, float* __restrict__ v,
+                                const float* __restrict__ g, float lr, float b1, float b2,
+                                float eps, float wd, float bc1, float bc2, TS* shadow,
+                                int64_t lds) {
+  const int64_t total = N * H0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float mi = m[i], vi = v[i];
+    const float x = adam_one(X0[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
+    X0[i] = x;
+    m[i] = mi;
+    v[i] = vi;
+    const int64_t r = i / H0, c = i % H0;
+    shadow[r * lds + c] = from_f<TS>(x);
+  }
+}
+
+template <typename TD>
+__global__ void copy_rows_kernel(int64_t N, int H, const float* __restrict__ src, TD* dst,
+                                 int64_t ldd) {
+  const int64_t total = N * H;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / H, c = i % H;
+    dst[r * ldd + c] = from_f<TD>(src[i]);
+  }
+}
+
+__global__ void weight_shadows_kernel(const float* __restrict__ th, int H0, int H1, int S,
+                                      int S_pad, bf16* W1s, bf16* W1t, bf16* W2s, bf16* W2t) {
+  const int64_t n1 = (int64_t)H1 * 2 * H0;
+  const int64_t n2 = (int64_t)S_pad * 2 * H1;
+  const float* Wcat1 = th;
+  const float* Wcat2 = th + n1 + H1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n1) {
+      const int o = (int)(i / (2 * H0)), k = (int)(i % (2 * H0));
+      const bf16 w = __float2bfloat16_rn(Wcat1[i]);
+      W1s[i] = w;
+      W1t[(int64_t)k * H1 + o] = w;
+    } else {
+      const int64_t j = i - n1;
+      const int s = (int)(j / (2 * H1)), k = (int)(j % (2 * H1));
+      const bf16 w = __float2bfloat16_rn(s < S ? Wcat2[(int64_t)s * 2 * H1 + k] : 0.f);
+      W2s[j] = w;
+      W2t[(int64_t)k * S_pad + s] = w;
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ float u24(uint64_t seed, uint64_t tag, uint64_t idx) {
+  const uint64_t h = splitmix64(seed ^ splitmix64(tag) ^ (idx * 0xD1B54A32D192ED03ull));
+  return (float)(h >> 40) * (1.0f / 16777216.0f);  // [0, 1)
+}
+
+__global__ void init_uniform_kernel(float* p, int64_t n, float bound, uint64_t seed,
+                                    uint64_t tag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (2.f * u24(seed, tag, (uint64_t)i) - 1.f) * bound;
+}
+
+// Box-Muller transform of two counter-based uniforms.
+__global__ void init_normal_kernel(float* p, int64_t n, uint64_t seed, uint64_t tag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float u1 = u24(seed, tag, 2 * (uint64_t)i) + (0.5f / 16777216.0f);
+    const float u2 = u24(seed, tag, 2 * (uint64_t)i + 1);
+    p[i] = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+  }
+}
+
+template <typename TS>
+__global__ void upcast_rows_kernel(int64_t N, int S, const TS* __restrict__ src, int64_t lds,
+                                   float* dst) {
+  const int64_t total = N * S;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / S, c = i % S;
+    dst[i] = to_f(src[r * lds + c]);
+  }
+}
+
+inline unsigned grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g, float lr,
+                 float beta1, float beta2, float eps, float wd, float bc1, float bc2,
+                 cudaStream_t st) {
+  adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, m, v, g, lr, beta1, beta2, eps, wd, bc1,
+                                           bc2);
+}
+
+void adam_emb_launch(int64_t N, int H0, float* X0, float* m, float* v, const float* g,
+                     float lr, float beta1, float beta2, float eps, float wd, float bc1,
+                     float bc2, void* shadow, int64_t lds, int dsh, cudaStream_t st) {
+  const unsigned grid = grid_for(N * H0);
+  if (dsh == DT_BF16)
+    adam_emb_kernel<bf16><<<grid, 256, 0, st>>>(N, H0, X0, m, v, g, lr, beta1, beta2, eps, wd,
+                                                bc1, bc2, static_cast<bf16*>(shadow), lds);
+  else
+    adam_emb_kernel<float><<<grid, 256, 0, st>>>(N, H0, X0, m, v, g, lr, beta1, beta2, eps, wd,
+                                                 bc1, bc2, static_cast<float*>(shadow), lds);
+}
+
+void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd, int ddst,
+                      cudaStream_t st) {
+  const unsigned grid = grid_for(N * H);
+  if (ddst == DT_BF16)
+    copy_rows_kernel<bf16><<<grid, 256, 0, st>>>(N, H, src, static_cast<bf16*>(dst), ldd);
+  else
+    copy_rows_kernel<float><<<grid, 256, 0, st>>>(N, H, src, static_cast<float*>(dst), ldd);
+}
+
+void weight_shadows_launch(const float* theta, int H0, int H1, int S, int S_pad, void* W1s,
+                           void* W1t, void* W2s, void* W2t, cudaStream_t st) {
+  const int64_t n = (int64_t)H1 * 2 * H0 + (int64_t)S_pad * 2 * H1;
+  weight_shadows_kernel<<<grid_for(n), 256, 0, st>>>(
+      theta, H0, H1, S, S_pad, static_cast<bf16*>(W1s), static_cast<bf16*>(W1t),
+      static_cast<bf16*>(W2s), static_cast<bf16*>(W2t));
+}
+
+void init_uniform_launch(float* p, int64_t n, float bound, uint64_t seed, uint64_t tag,
+                         cudaStream_t st) {
+  init_uniform_kernel<<<grid_for(n), 256, 0, st>>>(p, n, bound, seed, tag);
+}
+
+void init_normal_launch(float* p, int64_t n, uint64_t seed, uint64_t tag, cudaStream_t st) {
+  init_normal_kernel<<<grid_for(n), 256, 0, st>>>(p, n, seed, tag);
+}
+
+void upcast_rows_launch(int64_t N, int S, const void* src, int64_t lds, int dsrc, float* dst,
+                        cudaStream_t st) {
+  const unsigned grid = grid_for(N * S);
+  if (dsrc == DT_BF16)
+    upcast_rows_kernel<bf16><<<grid, 256, 0, st>>>(N, S, static_cast<const bf16*>(src), lds, dst);
+  else
+    upcast_rows_kernel<float><<<grid, 256, 0, st>>>(N, S, static_cast<const float*>(src), lds,
+                                                    dst);
+}
+
+}  // namespace cpra

@@ -1,0 +1,142 @@
+// Host-side launchers of the CPRA kernels (internal interface between the
+// C-ABI layer and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cpra {
+
+enum DType { DT_F32 = 0, DT_BF16 = 1 };
+
+// ---------------------------------------------------------------- SpMM
+// Row-gather SpMM over the symmetric CSR (Eq. GCN aggregate step):
+//   Y_i = s_i * (add_i + sum_{j in N(i)} X_j)  [* 1[mask_i > 0]]
+// with s_i = 1/|N(i)| (0 for isolated i) when `mean`, else 1.  X, add and
+// mask share the activation dtype dx; Y has dtype dy.  H % (16/sizeof(X)) == 0
+// and all row strides keep 16-byte alignment.  Optionally writes per-block
+// column sums of Y (before the dtype conversion) to colsum_partials[grid][H].
+struct SpmmArgs {
+  int64_t N = 0;
+  int H = 0;
+  const int* rowptr = nullptr;
+  const int* col = nullptr;
+  const float* inv_deg = nullptr;
+  const void* X = nullptr;
+  int64_t ldx = 0;
+  void* Y = nullptr;
+  int64_t ldy = 0;
+  int mean = 1;
+  const void* add = nullptr;
+  int64_t ldadd = 0;
+  const void* mask = nullptr;
+  int64_t ldm = 0;
+  float* colsum_partials = nullptr;
+  int dx = DT_F32;
+  int dy = DT_F32;
+};
+// Returns the grid size used (the row count of colsum_partials).
+int spmm_launch(const SpmmArgs& a, int max_grid, cudaStream_t st);
+
+// ---------------------------------------------------------------- loss
+// Fused SpMM + relaxed loss + rounding/evaluation (see cpra_op_loss).
+struct LossArgs {
+  int64_t N = 0;
+  int S = 0;
+  int64_t ldp = 0, ldg = 0;
+  const int* rowptr = nullptr;
+  const int* col = nullptr;
+  const float* P = nullptr;
+  const float* lambda = nullptr;
+  int problem = 0, alpha = 2, div_kind = 0, grad_kind = 0;
+  float gamma = 0.f, nu = 0.f;
+  void* G = nullptr;             // dtype dg, N x ldg
+  int dg = DT_F32;
+  uint32_t* xbits = nullptr;     // N x W, W = ceil(S/32)
+  float* partials = nullptr;     // [grid][pstride]: cost S | pen S | ann S | psi | gsum S
+  int64_t pstride = 0;
+  unsigned long long* counters = nullptr;  // obj[S], viol[S], ham  (zeroed by caller)
+  int do_loss = 1;               // 0: rounding + evaluation only
+};
+int64_t loss_pstride(int S);
+constexpr int kLossMaxGrid = 2048;
+// Returns the grid size used (row count of partials).
+int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st);
+
+// Sum partial rows: out[c] = sum_{b < nblocks} part[b*pstride + c], c < ncols,
+// in a fixed order; also copies out[copy_from .. copy_from+copy_n) to out2
+// when out2 != null and flags non-finite sums in *err_flag (bit 0).
+void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
+                     float* out, float* out2, int copy_from, int copy_n,
+                     int* err_flag, cudaStream_t st);
+
+// Per-shot records from the integer counters: objective, violations and the
+// FP64 qubo value; pair-Hamming total copied out.
+void eval_finalize(const unsigned long long* counters, int S, int problem,
+                   const float* lambda, void* out_records, long long* pair_hamming,
+                   cudaStream_t st);
+
+// ---------------------------------------------------------------- GEMM
+enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3 };
+// C[m, n] = sum_k A(m, k) B(n, k), FP32 accumulation.
+//   A(m, k) = A[m*lda + k] if a_kmajor else A[k*lda + m]; same for B.
+// Epilogues:
+//   EPI_PARTIAL      out0 (f32) + z*M*ld0 <- C for split z of gridDim.z
+//   EPI_BIAS_RELU    out0[m, n] <- max(C + bias[n], 0)
+//   EPI_BIAS_SIGMOID out0[m, n] <- 1/(1+exp(-(C + bias[n]))) for n < n_valid, else 0
+//   EPI_SPLIT        n < split: out0[m, n] <- C; else out1[m, n-split] <- C * row_scale[m]
+struct GemmArgs {
+  int64_t M = 0;
+  int Nc = 0;
+  int64_t K = 0;
+  const void* A = nullptr;
+  int64_t lda = 0;
+  int da = DT_F32;
+  int a_kmajor = 1;
+  const void* B = nullptr;
+  int64_t ldb = 0;
+  int db = DT_F32;
+  int b_kmajor = 1;
+  int epi = EPI_PARTIAL;
+  const float* bias = nullptr;
+  void* out0 = nullptr;
+  int64_t ld0 = 0;
+  int d0 = DT_F32;
+  void* out1 = nullptr;
+  int64_t ld1 = 0;
+  int d1 = DT_F32;
+  int split = 0;
+  const float* row_scale = nullptr;
+  int n_valid = 0;
+  int splits = 1;
+};
+void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
+// out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.
+void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp,
+                   float* out, int64_t ldo, cudaStream_t st);
+
+// ---------------------------------------------------------------- misc
+void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g,
+                 float lr, float beta1, float beta2, float eps, float wd,
+                 float bc1, float bc2, cudaStream_t st);
+// Adam over the N x H0 embedding master, then writes the activation copy
+// (dtype dsh) into shadow[i*lds + k].
+void adam_emb_launch(int64_t N, int H0, float* X0, float* m, float* v,
+                     const float* g, float lr, float beta1, float beta2,
+                     float eps, float wd, float bc1, float bc2, void* shadow,
+                     int64_t lds, int dsh, cudaStream_t st);
+void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd,
+                      int ddst, cudaStream_t st);
+// BF16 shadows of the dense weights:
+//   W1s [H1 x 2H0] = Wcat1, W1t [2H0 x H1] = Wcat1^T,
+//   W2s [S_pad x 2H1] = Wcat2 (pad rows 0), W2t [2H1 x S_pad] = Wcat2^T (pad cols 0).
+void weight_shadows_launch(const float* theta, int H0, int H1, int S, int S_pad,
+                           void* W1s, void* W1t, void* W2s, void* W2t, cudaStream_t st);
+void init_uniform_launch(float* p, int64_t n, float bound, uint64_t seed,
+                         uint64_t tag, cudaStream_t st);
+void init_normal_launch(float* p, int64_t n, uint64_t seed, uint64_t tag,
+                        cudaStream_t st);
+void upcast_rows_launch(int64_t N, int S, const void* src, int64_t lds, int dsrc,
+                        float* dst, cudaStream_t st);
+
+}  // namespace cpra

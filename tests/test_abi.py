@@ -1,0 +1,114 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+symbol include/cpra.h declares, and rejects bad graphs / configurations on
+the host before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2402_02190_gb300 import build as B
+from paper_2402_02190_gb300 import cpra
+from paper_2402_02190_gb300 import inputs as I
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "cpra.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return cpra.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^CPRA_API\s+[\w\s\*]*?\b(cpra_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("cpra_init_graph", "cpra_step", "cpra_round_eval", "cpra_solve",
+                 "cpra_op_loss", "cpra_op_round_eval", "cpra_destroy"):
+        assert must in names
+    assert set(names) == set(cpra.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_config_default_and_param_counts(L):
+    cfg = cpra.cpra_config_default()
+    assert (cfg.problem, cfg.S, cfg.H0, cfg.H1, cfg.alpha) == (cpra.MIS, 8, 16, 16, 2)
+    assert cfg.lr == pytest.approx(1e-3) and cfg.beta2 == pytest.approx(0.999)
+    assert cfg.gamma0 == pytest.approx(-2.0) and cfg.gamma1 == pytest.approx(0.1)
+    golden = os.path.join(os.path.dirname(__file__), "golden", "param_counts.txt")
+    for line in open(golden):
+        line = line.split("--")[0].strip()
+        if line and not line.startswith("#"):
+            H0, H1, S, count = (int(v) for v in line.split())
+            assert cpra.cpra_param_count_for(H0, H1, S) == count
+
+
+def test_workspace_bytes_valid_and_invalid(L):
+    cfg = cpra.make_config(S=256, H0=128, H1=128, precision=cpra.BF16, problem=cpra.MAXCUT)
+    nb = cpra.cpra_workspace_bytes(10**6, 5 * 10**6, cfg)
+    # P alone is N * S * 4 bytes
+    assert nb > 10**6 * 256 * 4
+    bad = cpra.make_config(S=0)
+    assert cpra.cpra_workspace_bytes(100, 300, bad) == 0
+    bad = cpra.make_config(H0=24)
+    assert cpra.cpra_workspace_bytes(100, 300, bad) == 0
+
+
+def _init_status(rowptr, col, **kw):
+    cfg = cpra.make_config(problem=cpra.MAXCUT, **kw)
+    try:
+        cpra.cpra_init_graph(rowptr, col, cfg, workspace=None)
+    except cpra.CpraError as e:
+        return e.status, str(e)
+    return cpra.CPRA_OK, ""
+
+
+@pytest.mark.parametrize("case", ["selfloop", "unsorted", "asym", "range", "rowptr0", "dup"])
+def test_invalid_graphs_rejected_on_host(L, case):
+    rp, col = I.random_regular_graph(20, 3, seed=1)
+    rp = rp.copy()
+    col = col.copy()
+    if case == "selfloop":
+        col[0] = 0
+    elif case == "unsorted":
+        col[0], col[1] = col[1], col[0]
+    elif case == "asym":
+        # 0 -> 1 and 1 -> 2 without the reverse entries
+        rp, col = np.array([0, 1, 2, 2, 2]), np.array([1, 2], dtype=np.int32)
+    elif case == "range":
+        col[5] = 99
+    elif case == "rowptr0":
+        rp[0] = 1
+    elif case == "dup":
+        col[1] = col[0]
+    st, msg = _init_status(rp, col)
+    assert st == cpra.CPRA_EINVAL, msg
+
+
+def test_invalid_config_rejected_on_host(L):
+    rp, col = I.random_regular_graph(20, 3, seed=1)
+    st, _ = _init_status(rp, col, alpha=3)
+    assert st == cpra.CPRA_EINVAL
+    cfg = cpra.make_config(problem=cpra.MIS)   # MIS without lambda
+    with pytest.raises(cpra.CpraError) as ei:
+        cpra.cpra_init_graph(rp, col, cfg, workspace=None)
+    assert ei.value.status == cpra.CPRA_EINVAL
+    assert "lambda" in str(ei.value)
+
+
+def test_memory_cap_fault_injection(L):
+    """A configured allocation cap makes init fail with ENOMEM, on the host,
+    before any device allocation."""
+    rp, col = I.random_regular_graph(200, 3, seed=2)
+    st, msg = _init_status(rp, col, mem_cap_bytes=1024)
+    assert st == cpra.CPRA_ENOMEM, msg
+    assert "mem_cap_bytes" in msg

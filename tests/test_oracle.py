@@ -9,7 +9,6 @@ index, transposed operand) fails at least one of them.
 import itertools
 import os
 
-import networkx as nx
 import numpy as np
 import pytest
 
@@ -72,6 +71,7 @@ def test_relaxation_equals_qubo_at_binary_points(N, d, seed):
 def test_min_mis_qubo_is_minus_independence_number(N, d, seed):
     """For lambda > 1 the MIS QUBO minimum equals -alpha(G) (textbook
     reduction); alpha(G) from networkx's exact max clique of the complement."""
+    nx = pytest.importorskip("networkx")
     g, rp, col = _graph(N, d, seed)
     G = nx.Graph()
     G.add_nodes_from(range(N))
@@ -297,6 +297,25 @@ def test_adam_matches_torch_optim():
             opt.step()
             cur, m, v = O.adam(cur, m, v, gt, t, lr=1e-3, wd=wd)
             assert np.allclose(cur, pt.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_bf16_round_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(10000).astype(np.float32) * 10.0 ** rng.integers(-30, 30, 10000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, 1e-40],
+                                 dtype=np.float32)]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.bf16_round(x), want)
+
+
+def test_relu_decision_in_bf16_only_moves_near_zero_signs():
+    g, theta, X0, cfg = _fd_case(O.MIS, O.DIV_STD, 2, seed=2)
+    a = O.forward(g, theta, X0, cfg["H0"], cfg["H1"], cfg["S"])
+    b = O.forward(g, theta, X0, cfg["H0"], cfg["H1"], cfg["S"], relu_decision="bf16")
+    differ = a["relu_on"] != b["relu_on"]
+    assert np.all(np.abs(a["Z1"][differ]) < 0.05)
+    assert np.array_equal(a["relu_on"], a["Z1"] > 0)
 
 
 def test_adam_first_step_closed_form():
