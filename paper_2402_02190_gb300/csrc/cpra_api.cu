@@ -324,7 +324,9 @@ char* act_off(void* base, int64_t elems, const cpra_ctx* c) {
 }
 
 // Dense layer dispatch: tensor cores (BF16 form) or CUDA cores.
-void dense(cpra_ctx* c, const GemmArgs& g) {
+void dense(cpra_ctx* c, const GemmArgs& g0) {
+  GemmArgs g = g0;
+  g.err_flag = c->err_flag;
   if (c->use_tc && tc_gemm_supported(g)) {
     c->launches += tc_gemm_launch(g, c->num_sms, c->stream);
   } else {

@@ -1,16 +1,492 @@
-// Tensor-core dense layers (tcgen05 + TMA): not yet enabled in this build;
-// every dense layer runs on the CUDA-core kernel.
+// Tensor-core dense layers of the BF16 form (Eq. GCN combine step, App. C.1):
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in TMEM) fed by
+// TMA (cp.async.bulk.tensor, 128-byte swizzle), sm_103a.
+//
+// C[M x Nc] = A[M x K] * B[Nc x K]^T with both operands K-major.  The weight
+// operand B (at most 256 x 256 here) stays resident in shared memory for the
+// whole persistent kernel; 128-row tiles of A stream through a ring of
+// shared-memory stages.  Roles per CTA (one CTA per SM):
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      TMEM allocation + MMA issuer (one elected lane)
+//   warps 2..9  epilogue: TMEM -> registers -> bias / activation / split ->
+//               global, two warps per TMEM lane quarter (column halves)
+// Two TMEM accumulators alternate so the epilogue of tile i overlaps the
+// MMAs of tile i+1.  Every mbarrier wait is bounded: on expiry the kernel
+// records bit 1 in *err_flag, stops issuing, waits (bounded) for its own TMA
+// copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
 #include "tc_gemm.cuh"
 
 namespace cpra {
+namespace {
 
-bool tc_available() { return false; }
-bool tc_prepare(int, std::string* msg) {
-  if (msg) *msg = "tensor-core path not built";
+constexpr int kBM = 128;            // rows per tile (UMMA M)
+constexpr int kBK = 64;             // K elements per stage (128 bytes of BF16)
+constexpr int kStageBytes = kBM * kBK * 2;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  Gives up after
+// kSpinLimit polls or when another role has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t a = smem_u32(b);
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 1023u) == 1023u && *abort_flag) return false;
+  }
   return false;
 }
-bool tc_gemm_supported(const GemmArgs&) { return false; }
-int tc_gemm_launch(const GemmArgs&, int, cudaStream_t) { return 0; }
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                  // leading offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride offset between 8-row groups
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcParams {
+  int64_t M = 0;
+  int Nc = 0, K = 0, n_kb = 0, BN = 0, n_tiles_n = 0, stages = 0, tmem_cols = 0, acc_stride = 0;
+  int64_t m_tiles = 0;
+  uint32_t idesc = 0;
+  int epi = 0;
+  const float* bias = nullptr;
+  void* out0 = nullptr;
+  int64_t ld0 = 0;
+  int d0 = DT_BF16;
+  void* out1 = nullptr;
+  int64_t ld1 = 0;
+  int d1 = DT_BF16;
+  int split = 0;
+  const float* row_scale = nullptr;
+  int n_valid = 0;
+  int* err_flag = nullptr;
+};
+
+template <int N>
+__device__ __forceinline__ void store_vec(void* base, int dt, int64_t idx, const float* v) {
+  if (dt == DT_BF16) storeN<N>(static_cast<bf16*>(base) + idx, v);
+  else storeN<N>(static_cast<float*>(base) + idx, v);
+}
+
+// Epilogue of 16 consecutive columns n .. n+15 of one row.
+__device__ __forceinline__ void epilogue16(const TcParams& p, int64_t row, int n, float* v) {
+  switch (p.epi) {
+    case EPI_BIAS_RELU: {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + p.bias[n + j], 0.f);
+      store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
+      break;
+    }
+    case EPI_BIAS_SIGMOID: {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        v[j] = (n + j < p.n_valid) ? 1.0f / (1.0f + expf(-(v[j] + p.bias[n + j]))) : 0.f;
+      store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
+      break;
+    }
+    case EPI_SPLIT: {
+      if (n < p.split) {
+        store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
+      } else {
+        const float s = p.row_scale[row];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] *= s;
+        store_vec<16>(p.out1, p.d1, row * p.ld1 + (n - p.split), v);
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t b_kb_bytes = static_cast<uint32_t>(p.BN) * kBK * 2;
+  uint8_t* Bs = smem;
+  uint8_t* As = Bs + static_cast<size_t>(p.n_kb) * b_kb_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(As + static_cast<size_t>(p.stages) * kStageBytes);
+  uint64_t* empty = full + p.stages;
+  uint64_t* bfull = empty + p.stages;
+  uint64_t* tfull = bfull + 1;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x % p.n_tiles_n;
+  const int group = blockIdx.x / p.n_tiles_n;
+  const int groups = gridDim.x / p.n_tiles_n;
+  const int n0 = n_tile * p.BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(tfull + 0, 1);
+    mbar_init(tfull + 1, 1);
+    mbar_init(tempty + 0, kEpiWarps);
+    mbar_init(tempty + 1, kEpiWarps);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    if (p.err_flag) atomicOr(p.err_flag, 2);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      mbar_expect_tx(bfull, static_cast<uint32_t>(p.n_kb) * b_kb_bytes);
+      for (int kb = 0; kb < p.n_kb; ++kb)
+        tma_load_2d(Bs + static_cast<size_t>(kb) * b_kb_bytes, &tmB, bfull, kb * kBK, n0);
+      uint32_t armed = 0;        // bit s: stage s has been armed at least once
+      uint32_t last_par = 0;     // bit s: parity of the last arming of stage s
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups) {
+        for (int kb = 0; kb < p.n_kb; ++kb) {
+          if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full + stage, kStageBytes);
+          tma_load_2d(As + static_cast<size_t>(stage) * kStageBytes, &tmA, full + stage, kb * kBK,
+                      static_cast<int>(mt * kBM));
+          armed |= 1u << stage;
+          last_par = (last_par & ~(1u << stage)) | (phase << stage);
+          if (++stage == p.stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // let our own copies land before the CTA's shared memory goes away
+        for (int s = 0; s < p.stages; ++s)
+          if (armed & (1u << s)) {
+            const uint32_t a = smem_u32(full + s);
+            for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, (last_par >> s) & 1u); ++it) {
+            }
+          }
+        const uint32_t a = smem_u32(bfull);
+        for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, 0); ++it) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      bool ok = mbar_wait(bfull, 0, abort_flag);
+      if (!ok) give_up();
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups, ++it) {
+        const int acc = it & 1;
+        const uint32_t acc_par = (static_cast<uint32_t>(it) >> 1) & 1u;
+        if (!mbar_wait(tempty + acc, acc_par ^ 1u, abort_flag)) {
+          give_up();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * p.acc_stride);
+        for (int kb = 0; kb < p.n_kb; ++kb) {
+          if (!mbar_wait(full + stage, phase, abort_flag)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(As + static_cast<size_t>(stage) * kStageBytes);
+          const uint32_t b0 = smem_u32(Bs + static_cast<size_t>(kb) * b_kb_bytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            umma_bf16(d_tmem, desc_kmajor_sw128(a0 + 32 * k), desc_kmajor_sw128(b0 + 32 * k),
+                      p.idesc, (kb | k) != 0 ? 1u : 0u);
+          umma_commit(empty + stage);
+          if (++stage == p.stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) umma_commit(tfull + acc);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew = warp - 2;
+    const int quarter = warp & 3;                 // TMEM lanes this warp may read
+    const int half = ew >> 2;                     // which half of the columns
+    const int nch = p.BN / 16;                    // 16-column chunks, split between halves
+    const int h0 = (nch + 1) / 2;
+    const int c_begin = half ? h0 * 16 : 0;
+    const int c_end = half ? p.BN : h0 * 16;
+    int it = 0;
+    for (int64_t mt = group; mt < p.m_tiles; mt += groups, ++it) {
+      const int acc = it & 1;
+      const uint32_t acc_par = (static_cast<uint32_t>(it) >> 1) & 1u;
+      if (!mbar_wait(tfull + acc, acc_par, abort_flag)) {
+        if (lane == 0) give_up();
+        break;
+      }
+      tc_fence_after();
+      const int64_t row = mt * kBM + quarter * 32 + lane;
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                             static_cast<uint32_t>(acc * p.acc_stride);
+      for (int c = c_begin; c < c_end; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + static_cast<uint32_t>(c), v);
+        if (row < p.M) epilogue16(p, row, n0 + c, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + acc);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------- host
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_once;
+bool g_ok = false;
+int g_max_smem = 0;
+
+void init_driver() {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&g_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (major != 10 || minor != 3) return;  // this build carries sm_103a code only
+  if (cudaFuncSetAttribute(tc_gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           g_max_smem) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  g_ok = true;
+}
+
+// 2-D BF16 tensor map over a row-major matrix: inner extent `cols`
+// elements, `rows` rows, row pitch `ld` elements; box kBK x box_rows.
+bool make_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld,
+              int box_rows) {
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int pick_bn(int Nc) {
+  if (Nc <= 256) return Nc;
+  for (int bn = 256; bn >= 16; bn -= 16)
+    if (Nc % bn == 0) return bn;
+  return 0;
+}
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+bool tc_prepare(int, std::string* msg) {
+  std::call_once(g_once, init_driver);
+  if (!g_ok && msg) *msg = "tensor-core path unavailable (driver entry point or device)";
+  return g_ok;
+}
+
+bool tc_gemm_supported(const GemmArgs& g) {
+  if (!g_ok) return false;
+  if (g.da != DT_BF16 || g.db != DT_BF16 || !g.a_kmajor || !g.b_kmajor) return false;
+  if (g.epi != EPI_BIAS_RELU && g.epi != EPI_BIAS_SIGMOID && g.epi != EPI_SPLIT) return false;
+  if (g.K < kBK || g.K % 8 || g.lda % 8 || g.ldb % 8) return false;
+  if (g.Nc % 16 || pick_bn(g.Nc) == 0) return false;
+  if (g.epi == EPI_SPLIT && g.split % 16) return false;
+  if (g.ld0 % 8 || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
+  const int bn = pick_bn(g.Nc);
+  const int n_kb = static_cast<int>((g.K + kBK - 1) / kBK);
+  const size_t need = 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + 2 * kStageBytes + 256;
+  return need <= static_cast<size_t>(g_max_smem);
+}
+
+int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
+  TcParams p;
+  p.M = g.M;
+  p.Nc = g.Nc;
+  p.K = static_cast<int>(g.K);
+  p.BN = pick_bn(g.Nc);
+  p.n_tiles_n = g.Nc / p.BN;
+  p.n_kb = (p.K + kBK - 1) / kBK;
+  p.m_tiles = (g.M + kBM - 1) / kBM;
+  const size_t b_bytes = static_cast<size_t>(p.n_kb) * p.BN * kBK * 2;
+  const size_t fixed = 1024 + b_bytes + 256;
+  int stages = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / kStageBytes);
+  stages = stages > 8 ? 8 : stages;
+  p.stages = stages;
+  size_t smem = fixed + static_cast<size_t>(stages) * kStageBytes;
+  // at least 120 KB so that only one CTA (and one TMEM allocation) fits per SM
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  p.acc_stride = (p.BN + 31) / 32 * 32;
+  int cols = 32;
+  while (cols < 2 * p.acc_stride) cols <<= 1;
+  p.tmem_cols = cols;
+  p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(p.BN >> 3) << 17) |
+            (static_cast<uint32_t>(kBM >> 4) << 24);
+  p.epi = g.epi;
+  p.bias = g.bias;
+  p.out0 = g.out0;
+  p.ld0 = g.ld0;
+  p.d0 = g.d0;
+  p.out1 = g.out1;
+  p.ld1 = g.ld1;
+  p.d1 = g.d1;
+  p.split = g.split;
+  p.row_scale = g.row_scale;
+  p.n_valid = g.n_valid > 0 ? g.n_valid : g.Nc;
+  p.err_flag = g.err_flag;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, g.A, g.K, g.M, g.lda, kBM) || !make_map(&tb, g.B, g.K, g.Nc, g.ldb, p.BN)) {
+    gemm_simt_launch(g, st);  // descriptor rejected: same product on CUDA cores
+    return 1;
+  }
+  int groups = num_sms / p.n_tiles_n;
+  if (groups < 1) groups = 1;
+  const int64_t max_groups = p.m_tiles;
+  if (groups > max_groups) groups = static_cast<int>(max_groups);
+  const int grid = groups * p.n_tiles_n;
+  tc_gemm_nt_kernel<<<grid, kThreads, smem, st>>>(ta, tb, p);
+  return 1;
+}
+
 bool tc_wgrad_supported(const GemmArgs&) { return false; }
 int tc_wgrad_launch(const GemmArgs&, int, size_t, float*, int64_t, cudaStream_t) { return 0; }
 

@@ -109,6 +109,7 @@ struct GemmArgs {
   const float* row_scale = nullptr;
   int n_valid = 0;
   int splits = 1;
+  int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
 };
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
 // out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.
