@@ -33,7 +33,9 @@ ABI_FUNCTIONS = (
     "cpra_launch_count", "cpra_profile_enable", "cpra_profile_read", "cpra_kernel_name",
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
+    "cpra_op_loss_noalloc",
 )
+NOALLOC_MAX_S = 1024
 
 
 class CpraError(RuntimeError):
@@ -99,6 +101,8 @@ def lib():
         "cpra_op_loss_scratch_bytes": (sz, [i64, i32]),
         "cpra_op_loss": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, i32, f32, f32, i32, i32,
                                    vp, i64, vp, vp, vp, sz, vp]),
+        "cpra_op_loss_noalloc": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, i32, f32, f32,
+                                           i32, i32, vp, i64, vp, vp, vp]),
         "cpra_op_round_eval_scratch_bytes": (sz, [i32]),
         "cpra_op_round_eval": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, sz,
                                          vp]),
@@ -297,6 +301,26 @@ def cpra_op_loss(rowptr32, col32, P, lam, problem, alpha, gamma, nu, div_kind, g
         G.stride(0), C.c_void_p(x_bits.data_ptr()) if x_bits is not None else None,
         C.c_void_p(terms.data_ptr()), C.c_void_p(scratch.data_ptr()), scratch.numel(),
         _stream_handle(stream))
+    _check(st)
+
+
+def cpra_op_loss_noalloc(rowptr32, col32, P, lam, problem, alpha, gamma, nu, div_kind,
+                         grad_kind, G, x_bits, terms, stream=None):
+    """cpra_op_loss without a scratch argument, for callers that cannot
+    allocate device memory (the library keeps a fixed device array for its
+    partial sums).  S is limited to NOALLOC_MAX_S; calls must not overlap on
+    the GPU."""
+    N, S = P.shape[0], terms.numel() // 4
+    if S > NOALLOC_MAX_S:
+        raise CpraError(CPRA_EINVAL,
+                        f"S={S} exceeds the allocation-free limit of {NOALLOC_MAX_S} shots")
+    st = lib().cpra_op_loss_noalloc(
+        N, S, C.c_void_p(rowptr32.data_ptr()), C.c_void_p(col32.data_ptr()),
+        C.c_void_p(P.data_ptr()), P.stride(0),
+        C.c_void_p(lam.data_ptr()) if lam is not None else None, problem, alpha,
+        C.c_float(gamma), C.c_float(nu), div_kind, grad_kind, C.c_void_p(G.data_ptr()),
+        G.stride(0), C.c_void_p(x_bits.data_ptr()) if x_bits is not None else None,
+        C.c_void_p(terms.data_ptr()), _stream_handle(stream))
     _check(st)
 
 
