@@ -360,6 +360,7 @@ void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_
   const int64_t cap = (int64_t)(c->wg_part_floats / ((size_t)M * Nc));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, cap));
   g.splits = (int)splits;
+  g.err_flag = c->err_flag;
   if (c->use_tc && tc_wgrad_supported(g)) {
     c->launches += tc_wgrad_launch(g, c->num_sms, c->wg_part_floats, dst, ldo, c->stream);
     return;

@@ -362,6 +362,207 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   }
 }
 
+// ------------------------------------------------------- weight gradients
+// C[M x Nc] = sum_k A[k, m] B[k, n] with A, B row-major over k (the node
+// dimension): both operands are MN-major.  Shared-memory tiles hold 64 k-rows
+// of 128 bytes (64 elements of m or n) per TMA box, 128-byte swizzle; 64-wide
+// chunks along m / n are LBO = 8 KB apart and 8-row k groups SBO = 1 KB.
+// Each CTA owns up to two 128-row m chunks (two TMEM accumulators sharing
+// every B tile) times one n tile of width BN, over one contiguous slice of
+// k; it writes its FP32 partial tile to part[split][m][n] and a separate
+// kernel adds the slices in a fixed order.
+constexpr int kWgK = 64;             // k rows per stage
+constexpr int kBoxBytes = 64 * 128;  // one 64 x 64 BF16 box
+
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= static_cast<uint64_t>(kBoxBytes >> 4) << 16;       // leading offset: next 64-wide chunk
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;            // stride offset: next 8 k-rows
+  d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                    // 128-byte swizzle
+  return d;
+}
+
+struct WgParams {
+  int M = 0, Nc = 0, BN = 0, mpc = 0, m_groups = 0, n_tiles = 0, splits = 0, stages = 0;
+  int tmem_cols = 0, acc_stride = 0;
+  int64_t k_blocks = 0;  // ceil(K / 64)
+  uint32_t idesc = 0;
+  float* part = nullptr;
+  int* err_flag = nullptr;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_wgrad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const WgParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t a_bytes = static_cast<uint32_t>(p.mpc) * 2 * kBoxBytes;  // 128 m per chunk
+  const uint32_t b_bytes = static_cast<uint32_t>(p.BN / 64) * kBoxBytes;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(p.stages) * stage_bytes);
+  uint64_t* empty = full + p.stages;
+  uint64_t* tfull = empty + p.stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfull + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x % (p.m_groups * p.n_tiles);
+  const int split = blockIdx.x / (p.m_groups * p.n_tiles);
+  const int mg = tile % p.m_groups;
+  const int nt = tile / p.m_groups;
+  const int m_base = mg * p.mpc * 128;
+  const int n0 = nt * p.BN;
+  const int64_t per = (p.k_blocks + p.splits - 1) / p.splits;
+  const int64_t kb_begin = per * split;
+  const int64_t kb_end = kb_begin + per < p.k_blocks ? kb_begin + per : p.k_blocks;
+  const int64_t n_kb = kb_end > kb_begin ? kb_end - kb_begin : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    if (p.err_flag) atomicOr(p.err_flag, 2);
+  };
+
+  if (warp == 0) {
+    if (lane == 0 && n_kb > 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      // A boxes lying wholly past the last valid row m are not loaded: the
+      // accumulator rows they would feed are never stored.
+      int a_boxes = (p.M - m_base + 63) / 64;
+      if (a_boxes > 2 * p.mpc) a_boxes = 2 * p.mpc;
+      const uint32_t tx_bytes = static_cast<uint32_t>(a_boxes) * kBoxBytes + b_bytes;
+      uint32_t armed = 0, last_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t kb = kb_begin; kb < kb_end; ++kb) {
+        if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + static_cast<size_t>(stage) * stage_bytes;
+        mbar_expect_tx(full + stage, tx_bytes);
+        const int krow = static_cast<int>(kb * kWgK);
+        for (int j = 0; j < a_boxes; ++j)
+          tma_load_2d(st + static_cast<size_t>(j) * kBoxBytes, &tmA, full + stage, m_base + 64 * j,
+                      krow);
+        for (int j = 0; j < p.BN / 64; ++j)
+          tma_load_2d(st + a_bytes + static_cast<size_t>(j) * kBoxBytes, &tmB, full + stage,
+                      n0 + 64 * j, krow);
+        armed |= 1u << stage;
+        last_par = (last_par & ~(1u << stage)) | (phase << stage);
+        if (++stage == p.stages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (!ok) {
+        for (int s = 0; s < p.stages; ++s)
+          if (armed & (1u << s)) {
+            const uint32_t a = smem_u32(full + s);
+            for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, (last_par >> s) & 1u); ++it) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && n_kb > 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t kb = 0; kb < n_kb; ++kb) {
+        if (!mbar_wait(full + stage, phase, abort_flag)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t s0 = smem_u32(smem + static_cast<size_t>(stage) * stage_bytes);
+        const uint32_t b0 = s0 + a_bytes;
+#pragma unroll
+        for (int k = 0; k < kWgK / 16; ++k) {
+          for (int mc = 0; mc < p.mpc; ++mc)
+            umma_bf16(tmem_base + static_cast<uint32_t>(mc * p.acc_stride),
+                      desc_mnmajor_sw128(s0 + mc * 2 * kBoxBytes + k * 2048),
+                      desc_mnmajor_sw128(b0 + k * 2048), p.idesc, (kb | k) != 0 ? 1u : 0u);
+        }
+        umma_commit(empty + stage);
+        if (++stage == p.stages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (ok) umma_commit(tfull);
+    }
+  } else {
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int nch = p.BN / 16;
+    const int h0 = (nch + 1) / 2;
+    const int c_begin = half ? h0 * 16 : 0;
+    const int c_end = half ? p.BN : h0 * 16;
+    bool ok = true;
+    if (n_kb > 0) {
+      ok = mbar_wait(tfull, 0, abort_flag);
+      if (!ok && lane == 0) give_up();
+      tc_fence_after();
+    }
+    float* out = p.part + static_cast<int64_t>(split) * p.M * p.Nc;
+    for (int mc = 0; ok && mc < p.mpc; ++mc) {
+      const int m = m_base + mc * 128 + quarter * 32 + lane;
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                             static_cast<uint32_t>(mc * p.acc_stride);
+      for (int c = c_begin; c < c_end; c += 16) {
+        float v[16];
+        if (n_kb > 0) {
+          tmem_ld16(taddr + static_cast<uint32_t>(c), v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (m < p.M && n0 + c < p.Nc) storeN<16>(out + static_cast<int64_t>(m) * p.Nc + n0 + c, v);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
 // ------------------------------------------------------------------- host
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
@@ -385,6 +586,8 @@ void init_driver() {
   cudaDeviceGetAttribute(&g_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (major != 10 || minor != 3) return;  // this build carries sm_103a code only
   if (cudaFuncSetAttribute(tc_gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           g_max_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            g_max_smem) != cudaSuccess) {
     cudaGetLastError();
     return;
@@ -487,7 +690,79 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   return 1;
 }
 
-bool tc_wgrad_supported(const GemmArgs&) { return false; }
-int tc_wgrad_launch(const GemmArgs&, int, size_t, float*, int64_t, cudaStream_t) { return 0; }
+namespace {
+
+struct WgShape {
+  int BN, n_tiles, mpc, m_groups, stages;
+  uint32_t stage_bytes;
+};
+
+bool wg_shape(const GemmArgs& g, WgShape* s) {
+  const int nc64 = (g.Nc + 63) / 64 * 64;
+  s->BN = nc64 < 256 ? nc64 : 256;
+  s->n_tiles = (g.Nc + s->BN - 1) / s->BN;
+  const int m_chunks = static_cast<int>((g.M + 127) / 128);
+  s->mpc = m_chunks < 2 ? m_chunks : 2;
+  s->m_groups = (m_chunks + s->mpc - 1) / s->mpc;
+  s->stage_bytes = static_cast<uint32_t>(s->mpc) * 2 * kBoxBytes +
+                   static_cast<uint32_t>(s->BN / 64) * kBoxBytes;
+  const size_t fixed = 1024 + 256;
+  int st = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / s->stage_bytes);
+  s->stages = st > 8 ? 8 : st;
+  return s->stages >= 2;
+}
+
+}  // namespace
+
+bool tc_wgrad_supported(const GemmArgs& g) {
+  if (!g_ok) return false;
+  if (g.da != DT_BF16 || g.db != DT_BF16 || g.a_kmajor || g.b_kmajor) return false;
+  if (g.epi != EPI_PARTIAL || g.lda % 8 || g.ldb % 8 || g.Nc % 16) return false;
+  if (g.K < kWgK || g.M < 1) return false;
+  WgShape s;
+  return wg_shape(g, &s);
+}
+
+int tc_wgrad_launch(const GemmArgs& g, int num_sms, size_t part_floats, float* dst, int64_t ldo,
+                    cudaStream_t st) {
+  WgShape s;
+  wg_shape(g, &s);
+  WgParams p;
+  p.M = static_cast<int>(g.M);
+  p.Nc = g.Nc;
+  p.BN = s.BN;
+  p.mpc = s.mpc;
+  p.m_groups = s.m_groups;
+  p.n_tiles = s.n_tiles;
+  p.stages = s.stages;
+  p.acc_stride = s.BN;
+  int cols = 32;
+  while (cols < s.mpc * s.BN) cols <<= 1;
+  p.tmem_cols = cols;
+  p.k_blocks = (g.K + kWgK - 1) / kWgK;
+  const int tiles = s.m_groups * s.n_tiles;
+  int64_t splits = num_sms / tiles;
+  if (splits < 1) splits = 1;
+  if (splits > p.k_blocks) splits = p.k_blocks;
+  const int64_t cap = static_cast<int64_t>(part_floats / (static_cast<size_t>(p.M) * p.Nc));
+  if (splits > cap) splits = cap < 1 ? 1 : cap;
+  p.splits = static_cast<int>(splits);
+  p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+            (static_cast<uint32_t>(s.BN >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+  p.part = static_cast<float*>(g.out0);
+  p.err_flag = g.err_flag;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, g.A, g.M, g.K, g.lda, kWgK) || !make_map(&tb, g.B, g.Nc, g.K, g.ldb, kWgK)) {
+    gemm_simt_launch(g, st);
+    splitk_reduce(static_cast<float*>(g.out0), g.splits, p.M, p.Nc, p.Nc, dst, ldo, st);
+    return 2;
+  }
+  size_t smem = 1024 + static_cast<size_t>(s.stages) * s.stage_bytes + 256;
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  const int grid = tiles * p.splits;
+  tc_wgrad_kernel<<<grid, kThreads, smem, st>>>(ta, tb, p);
+  splitk_reduce(p.part, p.splits, p.M, p.Nc, p.Nc, dst, ldo, st);
+  return 2;
+}
 
 }  // namespace cpra
