@@ -45,6 +45,11 @@ WORKLOADS = {
     "mis_rrg5_n1e6_s256_h128_fp32": dict(graph="rrg", N=10**6, d=5, seed=5, problem=0, S=256,
                                          H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=0,
                                          div=0),
+    # same shape at N/5 (P = 205 MB, still larger than L2): the small case
+    # for full ncu captures
+    "mis_rrg5_n2e5_s256_h128_bf16": dict(graph="rrg", N=2 * 10**5, d=5, seed=5, problem=0, S=256,
+                                         H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
+                                         div=0),
     "mis_rrg20_n1e4_s100_h256_bf16": dict(graph="rrg", N=10**4, d=20, seed=2, problem=0, S=100,
                                           H=256, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
                                           div=0),

@@ -57,6 +57,7 @@ struct LossArgs {
   int64_t pstride = 0;
   unsigned long long* counters = nullptr;  // obj[S], viol[S], ham  (zeroed by caller)
   int do_loss = 1;               // 0: rounding + evaluation only
+  int* err_flag = nullptr;       // device word; bit 1 set if a bounded wait gave up
 };
 int64_t loss_pstride(int S);
 constexpr int kLossMaxGrid = 2048;
