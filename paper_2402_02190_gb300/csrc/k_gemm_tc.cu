@@ -144,54 +144,77 @@ struct TcParams {
   int* err_flag = nullptr;
 };
 
-template <int N>
-__device__ __forceinline__ void store_vec(void* base, int dt, int64_t idx, const float* v) {
-  if (dt == DT_BF16) storeN<N>(static_cast<bf16*>(base) + idx, v);
-  else storeN<N>(static_cast<float*>(base) + idx, v);
+// Output staging: each epilogue warp owns two buffers of 32 rows x 16
+// columns; a TMA tensor store writes a buffer out while the warp fills the
+// other one.
+constexpr int kStgBytes = 32 * 16 * 4;
+constexpr int kStgTotal = kEpiWarps * 2 * kStgBytes;
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1)
+      : "memory");
 }
 
-// Epilogue of 16 consecutive columns n .. n+15 of one row.
-__device__ __forceinline__ void epilogue16(const TcParams& p, int64_t row, int n, float* v) {
+// Epilogue arithmetic of 16 consecutive columns n .. n+15 of one row;
+// returns which output (0 / 1) they belong to and their column there.
+__device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n, float* v,
+                                          int* out_col) {
+  *out_col = n;
   switch (p.epi) {
     case EPI_BIAS_RELU: {
+      const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + p.bias[n + j], 0.f);
-      store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
-      break;
+      for (int j = 0; j < 4; ++j) {
+        const float4 b = __ldg(b4 + j);
+        v[4 * j + 0] = fmaxf(v[4 * j + 0] + b.x, 0.f);
+        v[4 * j + 1] = fmaxf(v[4 * j + 1] + b.y, 0.f);
+        v[4 * j + 2] = fmaxf(v[4 * j + 2] + b.z, 0.f);
+        v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.f);
+      }
+      return 0;
     }
     case EPI_BIAS_SIGMOID: {
+      const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        v[j] = (n + j < p.n_valid) ? 1.0f / (1.0f + expf(-(v[j] + p.bias[n + j]))) : 0.f;
-      store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
-      break;
+      for (int j = 0; j < 4; ++j) {
+        const float4 b = __ldg(b4 + j);
+        const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * j + e;
+          v[k] = (n + k < p.n_valid) ? __frcp_rn(1.0f + __expf(-(v[k] + bb[e]))) : 0.f;
+        }
+      }
+      return 0;
     }
     case EPI_SPLIT: {
-      if (n < p.split) {
-        store_vec<16>(p.out0, p.d0, row * p.ld0 + n, v);
-      } else {
-        const float s = p.row_scale[row];
+      if (n < p.split) return 0;
+      const float s = row < p.M ? p.row_scale[row] : 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] *= s;
-        store_vec<16>(p.out1, p.d1, row * p.ld1 + (n - p.split), v);
-      }
-      break;
+      for (int j = 0; j < 16; ++j) v[j] *= s;
+      *out_col = n - p.split;
+      return 1;
     }
     default:
-      break;
+      return 0;
   }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const TcParams p) {
+                  const __grid_constant__ CUtensorMap tmO0,
+                  const __grid_constant__ CUtensorMap tmO1, const TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const uint32_t b_kb_bytes = static_cast<uint32_t>(p.BN) * kBK * 2;
   uint8_t* Bs = smem;
   uint8_t* As = Bs + static_cast<size_t>(p.n_kb) * b_kb_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(As + static_cast<size_t>(p.stages) * kStageBytes);
+  uint8_t* Stg = As + static_cast<size_t>(p.stages) * kStageBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Stg + kStgTotal);
   uint64_t* empty = full + p.stages;
   uint64_t* bfull = empty + p.stages;
   uint64_t* tfull = bfull + 1;
@@ -329,6 +352,8 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const int h0 = (nch + 1) / 2;
     const int c_begin = half ? h0 * 16 : 0;
     const int c_end = half ? p.BN : h0 * 16;
+    uint8_t* stg = Stg + static_cast<size_t>(ew) * 2 * kStgBytes;
+    int sb = 0;
     int it = 0;
     for (int64_t mt = group; mt < p.m_tiles; mt += groups, ++it) {
       const int acc = it & 1;
@@ -338,18 +363,35 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         break;
       }
       tc_fence_after();
-      const int64_t row = mt * kBM + quarter * 32 + lane;
+      const int64_t row0 = mt * kBM + quarter * 32;
+      const int64_t row = row0 + lane;
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                              static_cast<uint32_t>(acc * p.acc_stride);
       for (int c = c_begin; c < c_end; c += 16) {
         float v[16];
         tmem_ld16(taddr + static_cast<uint32_t>(c), v);
-        if (row < p.M) epilogue16(p, row, n0 + c, v);
+        int col;
+        const int which = epilogue16(p, row, n0 + c, v, &col);
+        uint8_t* buf = stg + sb * kStgBytes;
+        // the tensor store that last read this buffer must be done with it
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        if ((which ? p.d1 : p.d0) == DT_BF16) storeN<16>(reinterpret_cast<bf16*>(buf) + lane * 16, v);
+        else storeN<16>(reinterpret_cast<float*>(buf) + lane * 16, v);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {  // rows past M are clipped by the tensor map
+          tma_store_2d(which ? &tmO1 : &tmO0, buf, col, static_cast<int>(row0));
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        sb ^= 1;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty + acc);
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -610,6 +652,22 @@ bool make_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int6
   return r == CUDA_SUCCESS;
 }
 
+// Output tensor map: `cols` valid columns of dtype dt, `rows` rows, row pitch
+// `ld` elements; box of 16 columns x 32 rows, no swizzle (epilogue staging).
+bool make_out_map(CUtensorMap* m, const void* base, int dt, int64_t cols, int64_t rows,
+                  int64_t ld) {
+  const int esz = dt == DT_BF16 ? 2 : 4;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
+  cuuint32_t box[2] = {16, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, dt == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int pick_bn(int Nc) {
   if (Nc <= 256) return Nc;
   for (int bn = 256; bn >= 16; bn -= 16)
@@ -637,7 +695,8 @@ bool tc_gemm_supported(const GemmArgs& g) {
   if (g.ld0 % 8 || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
   const int bn = pick_bn(g.Nc);
   const int n_kb = static_cast<int>((g.K + kBK - 1) / kBK);
-  const size_t need = 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + 2 * kStageBytes + 256;
+  const size_t need =
+      1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal + 2 * kStageBytes + 256;
   return need <= static_cast<size_t>(g_max_smem);
 }
 
@@ -651,9 +710,9 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.n_kb = (p.K + kBK - 1) / kBK;
   p.m_tiles = (g.M + kBM - 1) / kBM;
   const size_t b_bytes = static_cast<size_t>(p.n_kb) * p.BN * kBK * 2;
-  const size_t fixed = 1024 + b_bytes + 256;
+  const size_t fixed = 1024 + b_bytes + kStgTotal + 256;
   int stages = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / kStageBytes);
-  stages = stages > 8 ? 8 : stages;
+  stages = stages > 6 ? 6 : stages;
   p.stages = stages;
   size_t smem = fixed + static_cast<size_t>(stages) * kStageBytes;
   // at least 120 KB so that only one CTA (and one TMEM allocation) fits per SM
@@ -676,8 +735,15 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.row_scale = g.row_scale;
   p.n_valid = g.n_valid > 0 ? g.n_valid : g.Nc;
   p.err_flag = g.err_flag;
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, g.A, g.K, g.M, g.lda, kBM) || !make_map(&tb, g.B, g.K, g.Nc, g.ldb, p.BN)) {
+  CUtensorMap ta, tb, to0, to1;
+  const int64_t cols0 = g.epi == EPI_SPLIT ? g.split : g.Nc;
+  bool ok = make_map(&ta, g.A, g.K, g.M, g.lda, kBM) && make_map(&tb, g.B, g.K, g.Nc, g.ldb, p.BN) &&
+            make_out_map(&to0, g.out0, g.d0, cols0, g.M, g.ld0);
+  if (ok) {
+    if (g.epi == EPI_SPLIT) ok = make_out_map(&to1, g.out1, g.d1, g.Nc - g.split, g.M, g.ld1);
+    else to1 = to0;
+  }
+  if (!ok) {
     gemm_simt_launch(g, st);  // descriptor rejected: same product on CUDA cores
     return 1;
   }
@@ -686,7 +752,7 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   const int64_t max_groups = p.m_tiles;
   if (groups > max_groups) groups = static_cast<int>(max_groups);
   const int grid = groups * p.n_tiles_n;
-  tc_gemm_nt_kernel<<<grid, kThreads, smem, st>>>(ta, tb, p);
+  tc_gemm_nt_kernel<<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
   return 1;
 }
 
