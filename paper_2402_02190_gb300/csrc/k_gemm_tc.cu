@@ -8,8 +8,9 @@
 // shared-memory stages.  Roles per CTA (one CTA per SM):
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocation + MMA issuer (one elected lane)
-//   warps 2..9  epilogue: TMEM -> registers -> bias / activation / split ->
-//               global, two warps per TMEM lane quarter (column halves)
+//   warps 2..17 epilogue: TMEM -> registers -> bias / activation / split ->
+//               shared-memory staging -> TMA tensor store; four warps per
+//               TMEM lane quarter, each owning a quarter of the columns
 // Two TMEM accumulators alternate so the epilogue of tile i overlaps the
 // MMAs of tile i+1.  Every mbarrier wait is bounded: on expiry the kernel
 // records bit 1 in *err_flag, stops issuing, waits (bounded) for its own TMA
@@ -28,7 +29,7 @@ namespace {
 constexpr int kBM = 128;            // rows per tile (UMMA M)
 constexpr int kBK = 64;             // K elements per stage (128 bytes of BF16)
 constexpr int kStageBytes = kBM * kBK * 2;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;   // four per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
@@ -110,9 +111,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive FP32 columns of this thread's TMEM lane (issue only; pair
+// with tmem_wait_ld before reading v).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
       "%15}, [%16];"
@@ -120,7 +121,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  tmem_ld16_issue(taddr, r);
+  tmem_wait_ld();
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -160,10 +168,11 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
 
 // Epilogue arithmetic of 16 consecutive columns n .. n+15 of one row;
 // returns which output (0 / 1) they belong to and their column there.
+template <int EPI>
 __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n, float* v,
                                           int* out_col) {
   *out_col = n;
-  switch (p.epi) {
+  switch (EPI) {
     case EPI_BIAS_RELU: {
       const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
 #pragma unroll
@@ -203,6 +212,7 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
   }
 }
 
+template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ CUtensorMap tmO0,
@@ -347,11 +357,11 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
     const int quarter = warp & 3;                 // TMEM lanes this warp may read
-    const int half = ew >> 2;                     // which half of the columns
-    const int nch = p.BN / 16;                    // 16-column chunks, split between halves
-    const int h0 = (nch + 1) / 2;
-    const int c_begin = half ? h0 * 16 : 0;
-    const int c_end = half ? p.BN : h0 * 16;
+    constexpr int parts = kEpiWarps / 4;          // column parts per lane quarter
+    const int cq = ew >> 2;
+    const int nch = p.BN / 16;                    // 16-column chunks, split between parts
+    const int c_begin = 16 * (nch * cq / parts);
+    const int c_end = 16 * (nch * (cq + 1) / parts);
     uint8_t* stg = Stg + static_cast<size_t>(ew) * 2 * kStgBytes;
     int sb = 0;
     int it = 0;
@@ -367,24 +377,36 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int64_t row = row0 + lane;
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                              static_cast<uint32_t>(acc * p.acc_stride);
-      for (int c = c_begin; c < c_end; c += 16) {
-        float v[16];
-        tmem_ld16(taddr + static_cast<uint32_t>(c), v);
-        int col;
-        const int which = epilogue16(p, row, n0 + c, v, &col);
-        uint8_t* buf = stg + sb * kStgBytes;
-        // the tensor store that last read this buffer must be done with it
-        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        __syncwarp();
-        if ((which ? p.d1 : p.d0) == DT_BF16) storeN<16>(reinterpret_cast<bf16*>(buf) + lane * 16, v);
-        else storeN<16>(reinterpret_cast<float*>(buf) + lane * 16, v);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {  // rows past M are clipped by the tensor map
-          tma_store_2d(which ? &tmO1 : &tmO0, buf, col, static_cast<int>(row0));
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      for (int c2 = c_begin; c2 < c_end; c2 += 32) {
+        // two TMEM loads in flight per wait
+        uint32_t r[2][16];
+        const bool two = c2 + 16 < c_end;
+        tmem_ld16_issue(taddr + static_cast<uint32_t>(c2), r[0]);
+        if (two) tmem_ld16_issue(taddr + static_cast<uint32_t>(c2 + 16), r[1]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int c = c2 + 16 * h;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
+          int col;
+          const int which = epilogue16<EPI>(p, row, n0 + c, v, &col);
+          uint8_t* buf = stg + sb * kStgBytes;
+          // the tensor store that last read this buffer must be done with it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+          if ((which ? p.d1 : p.d0) == DT_BF16) storeN<16>(reinterpret_cast<bf16*>(buf) + lane * 16, v);
+          else storeN<16>(reinterpret_cast<float*>(buf) + lane * 16, v);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {  // rows past M are clipped by the tensor map
+            tma_store_2d(which ? &tmO1 : &tmO0, buf, col, static_cast<int>(row0));
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          sb ^= 1;
         }
-        sb ^= 1;
       }
       tc_fence_before();
       __syncwarp();
@@ -566,11 +588,11 @@ tc_wgrad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else {
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = ew >> 2;
+    constexpr int parts = kEpiWarps / 4;
+    const int cq = ew >> 2;
     const int nch = p.BN / 16;
-    const int h0 = (nch + 1) / 2;
-    const int c_begin = half ? h0 * 16 : 0;
-    const int c_end = half ? p.BN : h0 * 16;
+    const int c_begin = 16 * (nch * cq / parts);
+    const int c_end = 16 * (nch * (cq + 1) / parts);
     bool ok = true;
     if (n_kb > 0) {
       ok = mbar_wait(tfull, 0, abort_flag);
@@ -627,8 +649,12 @@ void init_driver() {
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   cudaDeviceGetAttribute(&g_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (major != 10 || minor != 3) return;  // this build carries sm_103a code only
-  if (cudaFuncSetAttribute(tc_gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           g_max_smem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_BIAS_RELU>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_BIAS_SIGMOID>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_SPLIT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
       cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            g_max_smem) != cudaSuccess) {
     cudaGetLastError();
@@ -752,7 +778,17 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   const int64_t max_groups = p.m_tiles;
   if (groups > max_groups) groups = static_cast<int>(max_groups);
   const int grid = groups * p.n_tiles_n;
-  tc_gemm_nt_kernel<<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+  switch (g.epi) {
+    case EPI_BIAS_RELU:
+      tc_gemm_nt_kernel<EPI_BIAS_RELU><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+    case EPI_BIAS_SIGMOID:
+      tc_gemm_nt_kernel<EPI_BIAS_SIGMOID><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+    default:
+      tc_gemm_nt_kernel<EPI_SPLIT><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+  }
   return 1;
 }
 
