@@ -130,6 +130,26 @@ CPRA_API cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* r
    synchronises and returns CPRA_ENUMERIC if a term is not finite. */
 CPRA_API cpra_status cpra_step(cpra_ctx* ctx, int64_t t, float* loss_terms_out);
 
+/* Differentiable form of the same computation (for autograd frameworks).
+ * cpra_forward copies theta (device float [param_count], flat layout of
+ * CPRA_T_THETA) and the node embeddings h^0 (device float [N x H0]) into the
+ * context, runs the GNN forward (Eq. GCN twice, App. C.1) and the fused loss
+ * at the given gamma (Eq. CPRA-loss-function-GNN-penalty / -variation) and
+ * writes terms_dev (device float [3S+2]): cost_s (S), pen_s (S), ann_s (S),
+ * Psi, then the total R = sum_s (cost_s + lambda_s pen_s) + gamma sum_s ann_s
+ * + nu Psi.  It also evaluates the rounded shots (cpra_round_eval reads it).
+ * cpra_backward runs the hand-written adjoint of the last cpra_forward and
+ * writes scale * dR/dtheta (device float [param_count]) and, unless
+ * grad_emb_dev is NULL, scale * dR/dh^0 (device float [N x H0]).  Neither
+ * call touches the Adam state or the step counter.  cpra_backward returns
+ * CPRA_ESTATE if no cpra_forward precedes it (cpra_step, cpra_set_tensor and
+ * cpra_set_state invalidate the forward).  Both are asynchronous on the
+ * context stream. */
+CPRA_API cpra_status cpra_forward(cpra_ctx* ctx, const float* theta_dev, const float* emb_dev,
+                                  float gamma, float* terms_dev);
+CPRA_API cpra_status cpra_backward(cpra_ctx* ctx, float scale, float* grad_theta_dev,
+                                   float* grad_emb_dev);
+
 /* Copies the evaluation of the most recent cpra_step (or, before any step,
    of a fresh forward pass) to the host.  out: host [S]; pair_hamming_sum:
    host int64 receiving sum_i k_i (S - k_i) = sum_{s<l} d_H(x_s, x_l)

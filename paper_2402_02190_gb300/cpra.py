@@ -33,7 +33,7 @@ ABI_FUNCTIONS = (
     "cpra_launch_count", "cpra_profile_enable", "cpra_profile_read", "cpra_kernel_name",
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
-    "cpra_op_loss_noalloc",
+    "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward",
 )
 NOALLOC_MAX_S = 1024
 
@@ -82,6 +82,8 @@ def lib():
         "cpra_workspace_bytes": (sz, [i64, i64, P_cfg]),
         "cpra_init_graph": (C.c_int, [C.POINTER(vp), i64, vp, vp, vp, P_cfg, vp, sz, vp]),
         "cpra_step": (C.c_int, [vp, i64, vp]),
+        "cpra_forward": (C.c_int, [vp, vp, vp, f32, vp]),
+        "cpra_backward": (C.c_int, [vp, f32, vp, vp]),
         "cpra_round_eval": (C.c_int, [vp, vp, vp, vp]),
         "cpra_solve": (C.c_int, [vp, i64, i64, vp, vp]),
         "cpra_tensor_bytes": (sz, [vp, i32]),
@@ -196,6 +198,18 @@ def cpra_step(ctx, t: int, want_terms: bool = False):
         return out
     _check(lib().cpra_step(ctx, t, None), ctx)
     return None
+
+
+def cpra_forward(ctx, theta, emb, gamma: float, terms) -> None:
+    """theta, emb, terms: torch CUDA float32 tensors (contiguous)."""
+    _check(lib().cpra_forward(ctx, C.c_void_p(theta.data_ptr()), C.c_void_p(emb.data_ptr()),
+                              C.c_float(gamma), C.c_void_p(terms.data_ptr())), ctx)
+
+
+def cpra_backward(ctx, scale: float, grad_theta, grad_emb=None) -> None:
+    _check(lib().cpra_backward(ctx, C.c_float(scale), C.c_void_p(grad_theta.data_ptr()),
+                               C.c_void_p(grad_emb.data_ptr()) if grad_emb is not None else None),
+           ctx)
 
 
 def _S_of(ctx):

@@ -133,6 +133,7 @@ struct cpra_ctx {
   int64_t opt_steps = 0;
   int64_t launches = 0;
   bool have_eval = false;
+  bool fwd_valid = false;  // a cpra_forward whose activations are still in place
   bool use_tc = false;
   std::string err;
 
@@ -445,7 +446,9 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
   return CPRA_OK;
 }
 
-cpra_status run_backward_and_update(cpra_ctx* c) {
+// Adjoint of the last forward: dR/dtheta into c->grad and, with emb_grad,
+// dR/dh^0 into c->gX0.
+cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
   const int64_t N = c->N;
   const int H0 = c->H0, H1 = c->H1;
   const int max_grid = c->num_sms * 8;
@@ -487,7 +490,7 @@ cpra_status run_backward_and_update(cpra_ctx* c) {
     Region r(c, K_WGRAD1);  // dWcat1 = G_Z1^T [X0|M1]
     wgrad(c, c->GHM, 2 * H1, H1, c->XM, 2 * H0, 2 * H0, c->grad + L.wcat1, 2 * H0);
   }
-  if (c->cfg.train_embedding) {
+  if (emb_grad) {
     {  // [G_X0a | G_M1/deg] = G_Z1 Wcat1
       Region r(c, K_GEMM_DGRAD1);
       GemmArgs g;
@@ -513,6 +516,13 @@ cpra_status run_backward_and_update(cpra_ctx* c) {
       c->launches += 1;
     }
   }
+  return CPRA_OK;
+}
+
+// Adam on theta (+ BF16 shadows) and, when trained, on the embeddings.
+cpra_status run_update(cpra_ctx* c) {
+  const int64_t N = c->N;
+  const int H0 = c->H0;
   const int64_t t = c->opt_steps + 1;
   const float bc1 = (float)(1.0 - std::pow((double)c->cfg.beta1, (double)t));
   const float bc2 = (float)(1.0 - std::pow((double)c->cfg.beta2, (double)t));
@@ -708,10 +718,13 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
 
 cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
   if (!c) return CPRA_EINVAL;
+  c->fwd_valid = false;
   const float gamma = gamma_at(c->cfg, t);
   cpra_status s = run_forward_and_loss(c, gamma, true);
   if (s != CPRA_OK) return s;
-  s = run_backward_and_update(c);
+  s = run_backward(c, c->cfg.train_embedding != 0);
+  if (s != CPRA_OK) return s;
+  s = run_update(c);
   if (s != CPRA_OK) return s;
   s = cuda_check(c, cudaGetLastError(), "step kernels");
   if (s != CPRA_OK) return s;
@@ -723,6 +736,43 @@ cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
     if (s != CPRA_OK) return s;
   }
   return CPRA_OK;
+}
+
+cpra_status cpra_forward(cpra_ctx* c, const float* theta_dev, const float* emb_dev, float gamma,
+                         float* terms_dev) {
+  if (!c || !theta_dev || !emb_dev || !terms_dev)
+    return c ? fail(c, CPRA_EINVAL, "cpra_forward: NULL pointer") : CPRA_EINVAL;
+  if (!std::isfinite(gamma)) return fail(c, CPRA_EINVAL, "cpra_forward: gamma must be finite");
+  cudaStream_t st = c->stream;
+  cpra_status s = cuda_check(c, cudaMemcpyAsync(c->theta, theta_dev, sizeof(float) * c->nparam,
+                                                cudaMemcpyDeviceToDevice, st), "theta");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpyAsync(c->X0m, emb_dev, sizeof(float) * c->N * c->H0,
+                                      cudaMemcpyDeviceToDevice, st), "embeddings");
+  if (s != CPRA_OK) return s;
+  refresh_shadows(c);
+  refresh_emb_shadow(c);
+  s = run_forward_and_loss(c, gamma, true);
+  if (s != CPRA_OK) return s;
+  total_loss_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S, gamma,
+                    c->cfg.nu, terms_dev, st);
+  c->launches += 1;
+  c->fwd_valid = true;
+  return cuda_check(c, cudaGetLastError(), "forward kernels");
+}
+
+cpra_status cpra_backward(cpra_ctx* c, float scale, float* grad_theta_dev, float* grad_emb_dev) {
+  if (!c || !grad_theta_dev) return c ? fail(c, CPRA_EINVAL, "cpra_backward: NULL pointer") : CPRA_EINVAL;
+  if (!c->fwd_valid) return fail(c, CPRA_ESTATE, "cpra_backward: no cpra_forward to differentiate");
+  cpra_status s = run_backward(c, grad_emb_dev != nullptr);
+  if (s != CPRA_OK) return s;
+  scale_copy_launch(c->nparam, scale, c->grad, grad_theta_dev, c->stream);
+  c->launches += 1;
+  if (grad_emb_dev) {
+    scale_copy_launch(c->N * c->H0, scale, c->gX0, grad_emb_dev, c->stream);
+    c->launches += 1;
+  }
+  return cuda_check(c, cudaGetLastError(), "backward kernels");
 }
 
 cpra_status cpra_round_eval(cpra_ctx* c, cpra_shot_eval* out, int64_t* pair_hamming_sum,
@@ -870,6 +920,7 @@ cpra_status cpra_set_tensor(cpra_ctx* c, int32_t which, const void* host, size_t
   cpra_status s = cuda_check(c, cudaMemcpyAsync(flat_ptr(c, which), host, nbytes,
                                                 cudaMemcpyHostToDevice, st), "set");
   if (s != CPRA_OK) return s;
+  c->fwd_valid = false;
   if (which == CPRA_T_THETA) refresh_shadows(c);
   if (which == CPRA_T_EMB) refresh_emb_shadow(c);
   c->have_eval = false;

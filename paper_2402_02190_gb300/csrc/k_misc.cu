@@ -127,6 +127,32 @@ __global__ void upcast_rows_kernel(int64_t N, int S, const TS* __restrict__ src,
   }
 }
 
+__global__ void total_loss_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
+                                  int S, float gamma, float nu, float* out) {
+  __shared__ double part[256];
+  double t = 0.0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const double pen = lambda ? (double)lambda[s] * (double)terms[S + s] : 0.0;
+    t += (double)terms[s] + pen + (double)gamma * (double)terms[2 * S + s];
+  }
+  part[threadIdx.x] = t;
+  for (int k = threadIdx.x; k < 3 * S + 1; k += blockDim.x) out[k] = terms[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) r += part[k];
+    r += (double)nu * (double)terms[3 * S];
+    out[3 * S + 1] = (float)r;
+  }
+}
+
+__global__ void scale_copy_kernel(int64_t n, float scale, const float* __restrict__ src,
+                                  float* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = scale * src[i];
+}
+
 inline unsigned grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -178,6 +204,15 @@ void init_uniform_launch(float* p, int64_t n, float bound, uint64_t seed, uint64
 
 void init_normal_launch(float* p, int64_t n, uint64_t seed, uint64_t tag, cudaStream_t st) {
   init_normal_kernel<<<grid_for(n), 256, 0, st>>>(p, n, seed, tag);
+}
+
+void total_loss_launch(const float* terms, const float* lambda, int S, float gamma, float nu,
+                       float* out, cudaStream_t st) {
+  total_loss_kernel<<<1, 256, 0, st>>>(terms, lambda, S, gamma, nu, out);
+}
+
+void scale_copy_launch(int64_t n, float scale, const float* src, float* dst, cudaStream_t st) {
+  scale_copy_kernel<<<grid_for(n), 256, 0, st>>>(n, scale, src, dst);
 }
 
 void upcast_rows_launch(int64_t N, int S, const void* src, int64_t lds, int dsrc, float* dst,

@@ -140,5 +140,12 @@ void init_normal_launch(float* p, int64_t n, uint64_t seed, uint64_t tag,
                         cudaStream_t st);
 void upcast_rows_launch(int64_t N, int S, const void* src, int64_t lds, int dsrc,
                         float* dst, cudaStream_t st);
+// out[0..3S] = terms[0..3S] (cost, pen, ann per shot, Psi) and
+// out[3S+1] = R = sum_s (cost_s + lambda_s pen_s) + gamma sum_s ann_s + nu Psi
+// (lambda NULL: no penalty term), summed in a fixed order in FP64.
+void total_loss_launch(const float* terms, const float* lambda, int S, float gamma, float nu,
+                       float* out, cudaStream_t st);
+// dst[i] = scale * src[i]
+void scale_copy_launch(int64_t n, float scale, const float* src, float* dst, cudaStream_t st);
 
 }  // namespace cpra
