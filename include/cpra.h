@@ -285,18 +285,19 @@ CPRA_API cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* row
  * pool or a fixed budget, and latency-critical paths where an allocation
  * (and the device synchronisation it can imply) is not acceptable.
  * Arguments and results are those of cpra_op_loss without the scratch
- * buffer: the kernel's per-block partial sums and counters live in a
- * fixed device array of about 8.4 MB inside the library, which every GPU
- * that loads the library holds until the process exits.
+ * buffer: the kernel's per-block partial sums live in a fixed device
+ * array of about 8.4 MB inside the library, which every GPU that loads the
+ * library holds until the process exits.
  *   - S must be <= CPRA_NOALLOC_MAX_S; larger S returns CPRA_EINVAL without
  *     launching anything.  N is not limited.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream
  *     capture.
  *   - Every call on a device shares the one array, which keeps the last
- *     call's contents; the counters are cleared on cuda_stream at the start
- *     of each call.  Calls that overlap on the GPU (unordered streams,
- *     concurrent host threads) race on the array: order them on one stream.
+ *     call's contents; each call writes every partial row before reading
+ *     it, so nothing needs clearing.  Calls that overlap on the GPU
+ *     (unordered streams, concurrent host threads) race on the array:
+ *     order them on one stream.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
 #define CPRA_NOALLOC_MAX_S 1024
 CPRA_API cpra_status cpra_op_loss_noalloc(int64_t N, int32_t S, const int32_t* rowptr,

@@ -42,13 +42,14 @@ enum KernelId {
   K_SPMM_BWD1,
   K_ADAM,
   K_ADAM_EMB,
+  K_EVAL,
   K_COUNT_
 };
 
 const char* kKernelNames[K_COUNT_] = {
     "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
     "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
-    "gemm_dgrad1", "spmm_bwd1",   "adam",       "adam_embedding"};
+    "gemm_dgrad1", "spmm_bwd1",   "adam",       "adam_embedding", "round_eval"};
 
 constexpr size_t kAlign = 256;
 
@@ -418,29 +419,35 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
     g.out0 = c->P; g.ld0 = c->S_pad; g.d0 = DT_F32; g.n_valid = c->S;
     dense(c, g);
   }
-  {  // fused SpMM + loss + rounding / integer evaluation
+  int grid = 0;
+  {  // fused SpMM + loss + rounding bits
     Region r(c, K_LOSS);
-    cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
-                    c->stream);
     LossArgs a;
     a.N = N; a.S = c->S; a.ldp = c->S_pad; a.ldg = c->S_pad;
     a.rowptr = c->rowptr; a.col = c->col; a.P = c->P; a.lambda = c->lambda_d;
     a.problem = c->cfg.problem; a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
     a.grad_kind = 0; a.gamma = gamma; a.nu = c->cfg.nu;
     a.G = c->GZ2; a.dg = c->act_dt; a.xbits = c->xbits;
-    a.partials = c->loss_part; a.pstride = c->pstride; a.counters = c->counters;
+    a.partials = c->loss_part; a.pstride = c->pstride; a.err_flag = c->err_flag;
     a.do_loss = do_loss ? 1 : 0;
-    const int grid = loss_launch(a, c->num_sms * 4, c->stream);
+    grid = loss_launch(a, c->num_sms * 4, c->stream);
     c->launches += 1;
-    Region r2(c, K_LOSS_FIN);
-    if (do_loss) {
-      colsum_finalize(c->loss_part, grid, c->pstride, 4 * c->S + 1, c->terms, c->grad + L.b2,
-                      3 * c->S + 1, c->S, c->err_flag, c->stream);
-      c->launches += 1;
-    }
+  }
+  if (do_loss) {  // per-shot loss terms, db2
+    Region r(c, K_LOSS_FIN);
+    colsum_finalize(c->loss_part, grid, c->pstride, 4 * c->S + 1, c->terms, c->grad + L.b2,
+                    3 * c->S + 1, c->S, c->err_flag, c->stream);
+    c->launches += 1;
+  }
+  {  // exact integer evaluation of the rounded shots
+    Region r(c, K_EVAL);
+    cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
+                    c->stream);
+    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits, c->cfg.problem, c->counters,
+                     c->num_sms * 8, c->stream);
     eval_finalize(c->counters, c->S, c->cfg.problem, c->lambda_d, c->eval_rec, c->ham_d,
                   c->stream);
-    c->launches += 1;
+    c->launches += 2;
   }
   c->have_eval = true;
   return CPRA_OK;
@@ -1088,10 +1095,7 @@ cpra_status cpra_op_loss(int64_t N, int32_t S, const int32_t* rowptr, const int3
   a.grad_kind = grad_kind; a.gamma = gamma; a.nu = nu; a.G = G; a.dg = DT_F32;
   a.xbits = x_bits; a.pstride = loss_pstride(S);
   a.partials = cv.take<float>((size_t)kLossMaxGrid * a.pstride);
-  a.counters = cv.take<unsigned long long>(2 * (size_t)S + 1);
   a.do_loss = 1;
-  if (cudaMemsetAsync(a.counters, 0, (2 * (size_t)S + 1) * sizeof(unsigned long long), st) != cudaSuccess)
-    return CPRA_ECUDA;
   const int grid = loss_launch(a, device_sm_count() * 4, st);
   colsum_finalize(a.partials, grid, a.pstride, 4 * S + 1, terms, nullptr, 0, 0, nullptr, st);
   return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
@@ -1117,12 +1121,14 @@ cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr, cons
   LossArgs a;
   a.N = N; a.S = S; a.ldp = ldp; a.ldg = round_up(S, 4); a.rowptr = rowptr; a.col = col; a.P = P;
   a.lambda = lambda; a.problem = problem; a.xbits = x_bits;
-  a.counters = static_cast<unsigned long long*>(counters);
   a.do_loss = 0;
-  if (cudaMemsetAsync(a.counters, 0, cpra_op_round_eval_scratch_bytes(S), st) != cudaSuccess)
+  auto* cnt = static_cast<unsigned long long*>(counters);
+  if (cudaMemsetAsync(cnt, 0, cpra_op_round_eval_scratch_bytes(S), st) != cudaSuccess)
     return CPRA_ECUDA;
-  loss_launch(a, device_sm_count() * 4, st);
-  eval_finalize(a.counters, S, problem, lambda, out, reinterpret_cast<long long*>(pair_hamming), st);
+  const int sms = device_sm_count();
+  loss_launch(a, sms * 4, st);  // rounding bits
+  eval_bits_launch(N, S, rowptr, col, x_bits, problem, cnt, sms * 8, st);
+  eval_finalize(cnt, S, problem, lambda, out, reinterpret_cast<long long*>(pair_hamming), st);
   return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
 }
 

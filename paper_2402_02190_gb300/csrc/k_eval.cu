@@ -1,0 +1,141 @@
+// Exact integer evaluation of the rounded shots from their packed bits
+// (App. C.2 rounding, Table objective-functions, Prop. 3.2).
+//
+// x_bits holds, per node, W = ceil(S/32) words; bit (s mod 32) of word s/32
+// is x_is.  A segment of G >= W lanes owns one node row, lane w its word w.
+// For every edge (i, j) with j > i the lane combines x_i[w] and x_j[w]
+// (AND for MIS violations, XOR for MaxCut cut edges) and adds the 32 bits to
+// bit-sliced vertical counters (five bit planes, one ripple-carry add per
+// edge); the planes are flushed to per-shot shared-memory counters before
+// they can overflow.  MIS set sizes add x_i[w] the same way; the pairwise
+// Hamming sum adds k_i (S - k_i) with k_i = popcount of row i.  All sums are
+// integers, so the result does not depend on the order of the atomics.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cpra {
+
+namespace {
+
+struct Planes {
+  uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
+  int n = 0;  // additions since the last flush (< 32)
+  __device__ __forceinline__ void add(uint32_t x) {
+    uint32_t t = p0 & x; p0 ^= x; x = t;
+    t = p1 & x; p1 ^= x; x = t;
+    t = p2 & x; p2 ^= x; x = t;
+    t = p3 & x; p3 ^= x; x = t;
+    p4 ^= x;
+    ++n;
+  }
+  // Adds the per-bit counts to cnt[0..31] and clears the planes.
+  __device__ __forceinline__ void flush(int* cnt) {
+    if ((p0 | p1 | p2 | p3 | p4) != 0u) {
+#pragma unroll 4
+      for (int b = 0; b < 32; ++b) {
+        const int c = ((p0 >> b) & 1u) | (((p1 >> b) & 1u) << 1) | (((p2 >> b) & 1u) << 2) |
+                      (((p3 >> b) & 1u) << 3) | (((p4 >> b) & 1u) << 4);
+        if (c) atomicAdd(cnt + b, c);
+      }
+    }
+    p0 = p1 = p2 = p3 = p4 = 0u;
+    n = 0;
+  }
+};
+
+template <int G, int PROBLEM>
+__global__ void __launch_bounds__(256)
+eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
+                 const int* __restrict__ col, const uint32_t* __restrict__ bits,
+                 unsigned long long* counters) {
+  __shared__ int scnt[2 * 1024];  // objective per shot, then violations per shot
+  __shared__ unsigned long long ham_s;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);
+  const unsigned smask = segment_mask<G>(lane);
+  const int segs_per_warp = 32 / G;
+  const int64_t segs_per_block = (int64_t)(blockDim.x >> 5) * segs_per_warp;
+  const int64_t first = (int64_t)blockIdx.x * segs_per_block +
+                        (threadIdx.x >> 5) * segs_per_warp + lane / G;
+  const int64_t stride = (int64_t)gridDim.x * segs_per_block;
+  const int Wpad = W * 32;
+  for (int k = threadIdx.x; k < 2 * Wpad; k += blockDim.x) scnt[k] = 0;
+  if (threadIdx.x == 0) ham_s = 0ull;
+  __syncthreads();
+
+  const bool active = sub < W;
+  int* cnt_obj = scnt + 32 * sub;
+  int* cnt_viol = scnt + Wpad + 32 * sub;
+  Planes obj, viol;
+  long long ham = 0;
+  for (int64_t i = first; i < N; i += stride) {
+    const uint32_t xi = active ? bits[i * W + sub] : 0u;
+    int k = __popc(xi);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) k += __shfl_xor_sync(smask, k, off);
+    if (sub == 0) ham += (long long)k * (long long)(S - k);
+    if (PROBLEM == 0) {
+      obj.add(xi);
+      if (obj.n == 31) obj.flush(cnt_obj);
+    }
+    const int beg = rowptr[i];
+    const int end = rowptr[i + 1];
+    for (int eb = beg; eb < end; eb += G) {
+      const int e = eb + sub;
+      const int jl = (e < end) ? col[e] : -1;
+      const int cnt = min(G, end - eb);
+      for (int t = 0; t < cnt; ++t) {
+        const int j = __shfl_sync(smask, jl, t, G);
+        if (j <= i) continue;  // each edge once, at its lower endpoint
+        const uint32_t xj = active ? bits[(int64_t)j * W + sub] : 0u;
+        if (PROBLEM == 0) {
+          viol.add(xi & xj);
+          if (viol.n == 31) viol.flush(cnt_viol);
+        } else {
+          obj.add(xi ^ xj);
+          if (obj.n == 31) obj.flush(cnt_obj);
+        }
+      }
+    }
+  }
+  if (active) {
+    obj.flush(cnt_obj);
+    viol.flush(cnt_viol);
+  }
+  if (ham) atomicAdd(&ham_s, (unsigned long long)ham);
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    if (scnt[s]) atomicAdd(&counters[s], (unsigned long long)scnt[s]);
+    if (scnt[Wpad + s]) atomicAdd(&counters[S + s], (unsigned long long)scnt[Wpad + s]);
+  }
+  if (threadIdx.x == 0 && ham_s) atomicAdd(&counters[2 * S], ham_s);
+}
+
+template <int G>
+void launch_g(int64_t N, int S, int W, const int* rowptr, const int* col, const uint32_t* bits,
+              int problem, unsigned long long* counters, int max_grid, cudaStream_t st) {
+  constexpr int threads = 256;
+  const int segs_per_block = (threads / 32) * (32 / G);
+  int64_t want = (N + segs_per_block - 1) / segs_per_block;
+  int grid = (int)(want < max_grid ? want : max_grid);
+  if (grid < 1) grid = 1;
+  if (problem == 0)
+    eval_bits_kernel<G, 0><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
+  else
+    eval_bits_kernel<G, 1><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
+}
+
+}  // namespace
+
+void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
+                      int problem, unsigned long long* counters, int max_grid, cudaStream_t st) {
+  const int W = (S + 31) / 32;
+  if (W <= 1) launch_g<1>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+  else if (W <= 2) launch_g<2>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+  else if (W <= 4) launch_g<4>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+  else if (W <= 8) launch_g<8>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+  else if (W <= 16) launch_g<16>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+  else launch_g<32>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
+}
+
+}  // namespace cpra

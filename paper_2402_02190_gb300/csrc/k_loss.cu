@@ -1,4 +1,4 @@
-// Fused SpMM + relaxed CPRA loss + rounding/integer evaluation.
+// Fused SpMM + relaxed CPRA loss + rounding.
 //
 // For each node i the lanes owning row i gather the neighbour rows P_j (S
 // floats each) and accumulate Q_i = (A P)_i in registers; Q is never written.
@@ -10,14 +10,14 @@
 //   ann    += 1 - (2P_is - 1)^alpha,  dR/dP += -2 alpha gamma (2P_is-1)^(alpha-1)
 //   Psi: row mean / variance over the S shots by lane shuffles (O(S) per
 //   node, Prop. 3.2), dR/dP += nu * dPsi/dP_is
-// and writes G = dR/dP * P (1 - P) (the sigmoid head's dR/dZ2).  The same
-// gathered values give the rounding x = 1[P > 0.5f] (App. C.2) of both ends
-// of every edge, so MIS violations / MaxCut cuts per shot are counted here
-// too, exactly, with integer reductions (each edge at its lower endpoint).
+// writes G = dR/dP * P (1 - P) (the sigmoid head's dR/dZ2), and packs the
+// rounding x = 1[P > 0.5f] (App. C.2) of row i into bits; the exact integer
+// evaluation of those bits runs in k_eval.cu.
 //
 // Two kernels share the per-row epilogue:
-//   loss_kernel         rows of up to 64 shots: segments of LPR < 32 lanes per
-//                       row, neighbour rows gathered straight into registers;
+//   loss_kernel         rows of up to 64 shots (and bit packing alone):
+//                       segments of LPR lanes per row, neighbour rows
+//                       gathered straight into registers;
 //   loss_kernel_staged  rows of more than 64 shots: one warp per row; each
 //                       warp bulk-copies (cp.async.bulk on one mbarrier per
 //                       row) a row's own and neighbour P rows into shared
@@ -39,149 +39,136 @@ constexpr uint32_t kLossSpinLimit = 1u << 26;
 template <int CPL>
 struct ShotAcc {
   float pc[CPL][4], pp[CPL][4], pa[CPL][4], pg[CPL][4];
-  int cobj[CPL][4], cviol[CPL][4];
   float psi;
-  long long ham;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        pc[c][e] = pp[c][e] = pa[c][e] = pg[c][e] = 0.f;
-        cobj[c][e] = cviol[c][e] = 0;
-      }
+      for (int e = 0; e < 4; ++e) pc[c][e] = pp[c][e] = pa[c][e] = pg[c][e] = 0.f;
     psi = 0.f;
-    ham = 0;
   }
 };
 
-// Everything after Q_i is known: pairwise-Hamming term, rounded bits, row
-// statistics, dR/dP and the per-shot partial sums; stores G.
-template <int LPR, int CPL, int PROBLEM, typename TG, bool DO_LOSS>
-__device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int sub, unsigned smask,
-                                             const float (&p)[CPL][4], const float (&q)[CPL][4],
-                                             const bool (&xi)[CPL][4], int kones, float deg,
-                                             const float (&lam)[CPL][4], ShotAcc<CPL>& acc) {
+// Rounded bits of row i: bit (s mod 32) of word s/32 is 1[P_is > 0.5f].
+template <int LPR, int CPL>
+__device__ __forceinline__ void store_bits(const LossArgs& a, int64_t i, int sub, unsigned smask,
+                                           const float (&p)[CPL][4]) {
   const int S = a.S;
-  // pairwise Hamming contribution k_i (S - k_i) (Prop. 3.2)
+  const int W = (S + 31) / 32;
 #pragma unroll
-  for (int off = LPR / 2; off > 0; off >>= 1) kones += __shfl_xor_sync(smask, kones, off);
-  if (sub == 0) acc.ham += (long long)kones * (long long)(S - kones);
-
-  if (a.xbits) {
-    const int W = (S + 31) / 32;
+  for (int c = 0; c < CPL; ++c) {
+    uint32_t nib = 0;
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      uint32_t nib = 0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) nib |= (xi[c][e] ? 1u : 0u) << e;
-      uint32_t word = nib << ((sub & 7) * 4);
-      if constexpr (LPR >= 8) {
-        word = seg_or<8>(word, smask);
-      } else {
-        word = seg_or<LPR>(word, smask);
-      }
-      const int widx = (c * LPR + (sub & ~7)) / 8;
-      if ((sub & 7) == 0 && widx < W) a.xbits[i * W + widx] = word;
-    }
-  }
-
-  if constexpr (DO_LOSS) {
-    const int nchG = (int)(a.ldg / 4);
-    // Row statistics over the S shots: Psi is reported even when nu = 0.
-    float sum = 0.f, mx = -INFINITY, mn = INFINITY;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if ((c * LPR + sub) * 4 + e < S) {
-          sum += p[c][e];
-          mx = fmaxf(mx, p[c][e]);
-          mn = fminf(mn, p[c][e]);
-        }
-    sum = seg_sum<LPR>(sum, smask);
-    mx = seg_max<LPR>(mx, smask);
-    mn = seg_min<LPR>(mn, smask);
-    const float inv_S = 1.0f / (float)S;
-    const float mean = sum * inv_S;
-    float d2 = 0.f;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if ((c * LPR + sub) * 4 + e < S) {
-          const float d = p[c][e] - mean;
-          d2 += d * d;
-        }
-    d2 = seg_sum<LPR>(d2, smask);
-    const bool zero_var = (mx == mn);
-    const float var = zero_var ? 0.f : d2 * inv_S;
-    float rstd = 0.f;
-    if (a.div_kind == 0) {
-      rstd = zero_var ? 0.f : rsqrtf(var);
-      if (sub == 0) acc.psi += -(float)S * sqrtf(var);
+    for (int e = 0; e < 4; ++e)
+      nib |= (((c * LPR + sub) * 4 + e < S && p[c][e] > 0.5f) ? 1u : 0u) << e;
+    uint32_t word = nib << ((sub & 7) * 4);
+    if constexpr (LPR >= 8) {
+      word = seg_or<8>(word, smask);
     } else {
-      if (sub == 0) acc.psi += -(float)S * (float)S * var;
+      word = seg_or<LPR>(word, smask);
     }
-    const float c_ann = -2.f * (float)a.alpha * a.gamma;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int ch = c * LPR + sub;
-      if (ch >= nchG) continue;
-      float out[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int s = ch * 4 + e;
-        const float pv = p[c][e], qv = q[c][e];
-        float g;
-        if (PROBLEM == 0) {
-          g = -1.f + lam[c][e] * qv;
-        } else {
-          g = 2.f * qv - deg;
-        }
-        const float t = 2.f * pv - 1.f;
-        float tp = t;  // t^(alpha-1)
-        if (a.alpha != 2)
-          for (int r = 2; r < a.alpha; ++r) tp *= t;
-        g += c_ann * tp;
-        if (a.nu != 0.f) {
-          const float d = pv - mean;
-          g += a.nu * ((a.div_kind == 0) ? -d * rstd : -2.f * (float)S * d);
-        }
-        if (a.grad_kind == 0) g *= pv * (1.f - pv);
-        if (s < S) {
-          if (PROBLEM == 0) {
-            acc.pc[c][e] -= pv;
-            acc.pp[c][e] += 0.5f * pv * qv;
-          } else {
-            acc.pc[c][e] += pv * qv - deg * pv;
-          }
-          acc.pa[c][e] += 1.f - tp * t;
-          acc.pg[c][e] += g;
-        } else {
-          g = 0.f;
-        }
-        out[e] = g;
-      }
-      storeN<4>(static_cast<TG*>(a.G) + i * a.ldg + ch * 4, out);
-    }
+    const int widx = (c * LPR + (sub & ~7)) / 8;
+    if ((sub & 7) == 0 && widx < W) a.xbits[i * W + widx] = word;
   }
 }
 
-// Block-level reductions: integer counters through shared-memory atomics
-// and one global atomic per shot; float partials per shot in a fixed order
+// Everything after Q_i is known: row statistics, dR/dP and the per-shot
+// partial sums; stores G.
+template <int LPR, int CPL, int PROBLEM, typename TG>
+__device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int sub, unsigned smask,
+                                             const float (&p)[CPL][4], const float (&q)[CPL][4],
+                                             float deg, const float (&lam)[CPL][4],
+                                             ShotAcc<CPL>& acc) {
+  const int S = a.S;
+  const int nchG = (int)(a.ldg / 4);
+  // Row statistics over the S shots: Psi is reported even when nu = 0.
+  float sum = 0.f, mx = -INFINITY, mn = INFINITY;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((c * LPR + sub) * 4 + e < S) {
+        sum += p[c][e];
+        mx = fmaxf(mx, p[c][e]);
+        mn = fminf(mn, p[c][e]);
+      }
+  sum = seg_sum<LPR>(sum, smask);
+  mx = seg_max<LPR>(mx, smask);
+  mn = seg_min<LPR>(mn, smask);
+  const float inv_S = 1.0f / (float)S;
+  const float mean = sum * inv_S;
+  float d2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((c * LPR + sub) * 4 + e < S) {
+        const float d = p[c][e] - mean;
+        d2 += d * d;
+      }
+  d2 = seg_sum<LPR>(d2, smask);
+  const bool zero_var = (mx == mn);
+  const float var = zero_var ? 0.f : d2 * inv_S;
+  float rstd = 0.f;
+  if (a.div_kind == 0) {
+    rstd = zero_var ? 0.f : rsqrtf(var);
+    if (sub == 0) acc.psi += -(float)S * sqrtf(var);
+  } else {
+    if (sub == 0) acc.psi += -(float)S * (float)S * var;
+  }
+  const float c_ann = -2.f * (float)a.alpha * a.gamma;
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int ch = c * LPR + sub;
+    if (ch >= nchG) continue;
+    float out[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int s = ch * 4 + e;
+      const float pv = p[c][e], qv = q[c][e];
+      float g;
+      if (PROBLEM == 0) {
+        g = -1.f + lam[c][e] * qv;
+      } else {
+        g = 2.f * qv - deg;
+      }
+      const float t = 2.f * pv - 1.f;
+      float tp = t;  // t^(alpha-1)
+      if (a.alpha != 2)
+        for (int r = 2; r < a.alpha; ++r) tp *= t;
+      g += c_ann * tp;
+      if (a.nu != 0.f) {
+        const float d = pv - mean;
+        g += a.nu * ((a.div_kind == 0) ? -d * rstd : -2.f * (float)S * d);
+      }
+      if (a.grad_kind == 0) g *= pv * (1.f - pv);
+      if (s < S) {
+        if (PROBLEM == 0) {
+          acc.pc[c][e] -= pv;
+          acc.pp[c][e] += 0.5f * pv * qv;
+        } else {
+          acc.pc[c][e] += pv * qv - deg * pv;
+        }
+        acc.pa[c][e] += 1.f - tp * t;
+        acc.pg[c][e] += g;
+      } else {
+        g = 0.f;
+      }
+      out[e] = g;
+    }
+    storeN<4>(static_cast<TG*>(a.G) + i * a.ldg + ch * 4, out);
+  }
+}
+
+// Block-level reduction of the float partials per shot, in a fixed order,
 // into this block's partial row.
-template <int LPR, int CPL, bool DO_LOSS>
-__device__ __forceinline__ void block_reduce(const LossArgs& a, ShotAcc<CPL>& acc, float* red,
-                                             int* icnt, unsigned long long* ham_s) {
+template <int LPR, int CPL>
+__device__ __forceinline__ void block_reduce(const LossArgs& a, ShotAcc<CPL>& acc, float* red) {
   const int S = a.S;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LPR - 1);
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  __syncthreads();
-  for (int k = threadIdx.x; k < 2 * S; k += blockDim.x) icnt[k] = 0;
-  if (threadIdx.x == 0) *ham_s = 0ull;
   __syncthreads();
 #pragma unroll
   for (int c = 0; c < CPL; ++c)
@@ -189,118 +176,55 @@ __device__ __forceinline__ void block_reduce(const LossArgs& a, ShotAcc<CPL>& ac
     for (int e = 0; e < 4; ++e)
 #pragma unroll
       for (int off = LPR; off < 32; off <<= 1) {
-        acc.cobj[c][e] += __shfl_xor_sync(0xffffffffu, acc.cobj[c][e], off);
-        acc.cviol[c][e] += __shfl_xor_sync(0xffffffffu, acc.cviol[c][e], off);
-        if constexpr (DO_LOSS) {
-          acc.pc[c][e] += __shfl_xor_sync(0xffffffffu, acc.pc[c][e], off);
-          acc.pp[c][e] += __shfl_xor_sync(0xffffffffu, acc.pp[c][e], off);
-          acc.pa[c][e] += __shfl_xor_sync(0xffffffffu, acc.pa[c][e], off);
-          acc.pg[c][e] += __shfl_xor_sync(0xffffffffu, acc.pg[c][e], off);
-        }
+        acc.pc[c][e] += __shfl_xor_sync(0xffffffffu, acc.pc[c][e], off);
+        acc.pp[c][e] += __shfl_xor_sync(0xffffffffu, acc.pp[c][e], off);
+        acc.pa[c][e] += __shfl_xor_sync(0xffffffffu, acc.pa[c][e], off);
+        acc.pg[c][e] += __shfl_xor_sync(0xffffffffu, acc.pg[c][e], off);
       }
-  if (lane < LPR) {
-#pragma unroll
-    for (int c = 0; c < CPL; ++c)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int s = (c * LPR + sub) * 4 + e;
-        if (s < S) {
-          if (acc.cobj[c][e]) atomicAdd(&icnt[s], acc.cobj[c][e]);
-          if (acc.cviol[c][e]) atomicAdd(&icnt[S + s], acc.cviol[c][e]);
-        }
-      }
-  }
-  if (acc.ham) atomicAdd(ham_s, (unsigned long long)acc.ham);
-  float psi = 0.f;
-  if constexpr (DO_LOSS) psi = seg_sum<32>(acc.psi, 0xffffffffu);
+  const float psi = seg_sum<32>(acc.psi, 0xffffffffu);
+  float* outp = a.partials + (int64_t)blockIdx.x * a.pstride;
+  if (lane == 0) red[warp] = psi;
   __syncthreads();
-  for (int k = threadIdx.x; k < 2 * S; k += blockDim.x)
-    if (icnt[k]) atomicAdd(&a.counters[k], (unsigned long long)icnt[k]);
-  if (threadIdx.x == 0 && *ham_s) atomicAdd(&a.counters[2 * S], *ham_s);
-
-  if constexpr (DO_LOSS) {
-    float* outp = a.partials + (int64_t)blockIdx.x * a.pstride;
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarps; ++w) t += red[w];
+    outp[3 * S] = t;
+  }
+  for (int qd = 0; qd < 4; ++qd) {
     __syncthreads();
-    if (lane == 0) red[warp] = psi;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float t = 0.f;
-      for (int w = 0; w < nwarps; ++w) t += red[w];
-      outp[3 * S] = t;
-    }
-    for (int qd = 0; qd < 4; ++qd) {
-      __syncthreads();
-      if (lane < LPR) {
+    if (lane < LPR) {
 #pragma unroll
-        for (int c = 0; c < CPL; ++c)
+      for (int c = 0; c < CPL; ++c)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int s = (c * LPR + sub) * 4 + e;
-            if (s < S) {
-              const float v = qd == 0 ? acc.pc[c][e]
-                              : qd == 1 ? acc.pp[c][e]
-                              : qd == 2 ? acc.pa[c][e]
-                                        : acc.pg[c][e];
-              red[warp * S + s] = v;
-            }
+        for (int e = 0; e < 4; ++e) {
+          const int s = (c * LPR + sub) * 4 + e;
+          if (s < S) {
+            const float v = qd == 0 ? acc.pc[c][e]
+                            : qd == 1 ? acc.pp[c][e]
+                            : qd == 2 ? acc.pa[c][e]
+                                      : acc.pg[c][e];
+            red[warp * S + s] = v;
           }
-      }
-      __syncthreads();
-      const int base = qd < 3 ? qd * S : 3 * S + 1;
-      for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        float t = 0.f;
-        for (int w = 0; w < nwarps; ++w) t += red[w * S + s];
-        outp[base + s] = t;
-      }
+        }
+    }
+    __syncthreads();
+    const int base = qd < 3 ? qd * S : 3 * S + 1;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      float t = 0.f;
+      for (int w = 0; w < nwarps; ++w) t += red[w * S + s];
+      outp[base + s] = t;
     }
   }
 }
 
-template <int LPR, int CPL, int PROBLEM, bool DO_LOSS>
+template <int LPR, int CPL, int PROBLEM>
 __device__ __forceinline__ void load_lambda(const LossArgs& a, int sub, float (&lam)[CPL][4]) {
 #pragma unroll
   for (int c = 0; c < CPL; ++c)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int s = (c * LPR + sub) * 4 + e;
-      lam[c][e] = (PROBLEM == 0 && DO_LOSS && s < a.S) ? a.lambda[s] : 0.f;
-    }
-}
-
-// Own row: values, rounding bits, MIS set-size counts.
-template <int LPR, int CPL, int PROBLEM>
-__device__ __forceinline__ int own_row(const float (&p)[CPL][4], int sub, int S, bool (&xi)[CPL][4],
-                                       ShotAcc<CPL>& acc) {
-  int kones = 0;
-#pragma unroll
-  for (int c = 0; c < CPL; ++c)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int s = (c * LPR + sub) * 4 + e;
-      xi[c][e] = (s < S) && (p[c][e] > 0.5f);
-      kones += xi[c][e] ? 1 : 0;
-      if (PROBLEM == 0) acc.cobj[c][e] += xi[c][e] ? 1 : 0;
-    }
-  return kones;
-}
-
-// One gathered neighbour row (values f) of row i: Q accumulation and the
-// exact edge counts for edges (i, j) with j > i.
-template <int LPR, int CPL, int PROBLEM>
-__device__ __forceinline__ void take_neighbour(const float (&f)[CPL][4], bool upper, int sub, int S,
-                                               const bool (&xi)[CPL][4], float (&q)[CPL][4],
-                                               ShotAcc<CPL>& acc) {
-#pragma unroll
-  for (int c = 0; c < CPL; ++c)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      q[c][e] += f[c][e];
-      const bool xj = f[c][e] > 0.5f;
-      if (PROBLEM == 0) {
-        acc.cviol[c][e] += (upper && xi[c][e] && xj) ? 1 : 0;
-      } else {
-        acc.cobj[c][e] += (upper && (xi[c][e] != xj) && (c * LPR + sub) * 4 + e < S) ? 1 : 0;
-      }
+      lam[c][e] = (PROBLEM == 0 && s < a.S) ? a.lambda[s] : 0.f;
     }
 }
 
@@ -316,16 +240,12 @@ loss_kernel(LossArgs a) {
   const int64_t first = (int64_t)blockIdx.x * segs_per_block +
                         (threadIdx.x >> 5) * segs_per_warp + lane / LPR;
   const int64_t stride = (int64_t)gridDim.x * segs_per_block;
-  const int S = a.S;
-  const int nchS = (S + 3) / 4;
+  const int nchS = (a.S + 3) / 4;
   const float* __restrict__ P = a.P;
-
   extern __shared__ float red[];  // [nwarps][S]
-  __shared__ int icnt[2 * 1024];
-  __shared__ unsigned long long ham_s;
 
   float lam[CPL][4];
-  load_lambda<LPR, CPL, PROBLEM, DO_LOSS>(a, sub, lam);
+  if constexpr (DO_LOSS) load_lambda<LPR, CPL, PROBLEM>(a, sub, lam);
   ShotAcc<CPL> acc;
   acc.zero();
 
@@ -341,8 +261,8 @@ loss_kernel(LossArgs a) {
         for (int e = 0; e < 4; ++e) p[c][e] = 0.f;
       }
     }
-    bool xi[CPL][4];
-    const int kones = own_row<LPR, CPL, PROBLEM>(p, sub, S, xi, acc);
+    if (a.xbits) store_bits<LPR, CPL>(a, i, sub, smask, p);
+    if constexpr (!DO_LOSS) continue;
 
     float q[CPL][4];
 #pragma unroll
@@ -359,11 +279,10 @@ loss_kernel(LossArgs a) {
       int k = 0;
       for (; k + 4 <= cnt; k += 4) {
         uint4 raw[4][CPL];
-        int js[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          js[u] = __shfl_sync(smask, jl, k + u, LPR);
-          const float* row = P + (int64_t)js[u] * a.ldp;
+          const int j = __shfl_sync(smask, jl, k + u, LPR);
+          const float* row = P + (int64_t)j * a.ldp;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             const int ch = c * LPR + sub;
@@ -371,30 +290,33 @@ loss_kernel(LossArgs a) {
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float f[CPL][4];
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int c = 0; c < CPL; ++c) widen(raw[u][c], f[c], (const float*)nullptr);
-          take_neighbour<LPR, CPL, PROBLEM>(f, js[u] > i, sub, S, xi, q, acc);
-        }
+          for (int c = 0; c < CPL; ++c) {
+            float f[4];
+            widen(raw[u][c], f, (const float*)nullptr);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q[c][e] += f[e];
+          }
       }
       for (; k < cnt; ++k) {
         const int j = __shfl_sync(smask, jl, k, LPR);
         const float* row = P + (int64_t)j * a.ldp;
-        float f[CPL][4];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int ch = c * LPR + sub;
-          uint4 r = (ch < nchS) ? ldg_nc16(row + ch * 4) : make_uint4(0, 0, 0, 0);
-          widen(r, f[c], (const float*)nullptr);
+          if (ch < nchS) {
+            float f[4];
+            widen(ldg_nc16(row + ch * 4), f, (const float*)nullptr);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q[c][e] += f[e];
+          }
         }
-        take_neighbour<LPR, CPL, PROBLEM>(f, j > i, sub, S, xi, q, acc);
       }
     }
-    row_epilogue<LPR, CPL, PROBLEM, TG, DO_LOSS>(a, i, sub, smask, p, q, xi, kones,
-                                                 (float)(end - beg), lam, acc);
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, acc);
   }
-  block_reduce<LPR, CPL, DO_LOSS>(a, acc, red, icnt, &ham_s);
+  if constexpr (DO_LOSS) block_reduce<LPR, CPL>(a, acc, red);
 }
 
 // ---- staged variant: whole P rows bulk-copied into a per-warp ring ----
@@ -437,7 +359,7 @@ __device__ __forceinline__ void ring_copy(void* dst, const void* src, uint32_t b
 // single mbarrier (one wait per row).  While row r is processed, the rows
 // r + wstride .. r + (RS-1) wstride are in flight.  Neighbours beyond CAP
 // (high-degree rows) are gathered directly from global memory.
-template <int CPL, int PROBLEM, typename TG, bool DO_LOSS>
+template <int CPL, int PROBLEM, typename TG>
 __global__ void __launch_bounds__(256, 2)
 loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes) {
   constexpr int LPR = 32;
@@ -446,8 +368,7 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
   const unsigned smask = 0xffffffffu;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int S = a.S;
-  const int nchS = (S + 3) / 4;
+  const int nchS = (a.S + 3) / 4;
   const uint32_t row_bytes = (uint32_t)nchS * 16u;
 
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -461,7 +382,7 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
   __syncwarp();
 
   float lam[CPL][4];
-  load_lambda<LPR, CPL, PROBLEM, DO_LOSS>(a, sub, lam);
+  load_lambda<LPR, CPL, PROBLEM>(a, sub, lam);
   ShotAcc<CPL> acc;
   acc.zero();
 
@@ -509,7 +430,6 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
     const int beg = a.rowptr[i];
     const int end = a.rowptr[i + 1];
     const int n = min(end - beg, CAP);
-    const int jl = (lane < n) ? a.col[beg + lane] : 0;
     if (!ring_wait(bars + k, par)) {
       dead = true;
       break;
@@ -517,18 +437,18 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
     const unsigned char* base = slots + (size_t)k * rslot_bytes;
     float p[CPL][4];
     read_row(base, p);
-    bool xi[CPL][4];
-    const int kones = own_row<LPR, CPL, PROBLEM>(p, sub, S, xi, acc);
     float q[CPL][4];
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
 #pragma unroll
       for (int e = 0; e < 4; ++e) q[c][e] = 0.f;
     for (int t = 0; t < n; ++t) {
-      const int j = __shfl_sync(smask, jl, t);
       float f[CPL][4];
       read_row(base + (size_t)(1 + t) * row_bytes, f);
-      take_neighbour<LPR, CPL, PROBLEM>(f, j > i, sub, S, xi, q, acc);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q[c][e] += f[c][e];
     }
     __syncwarp();
     issue_row(next, k);  // refill the slot just read
@@ -538,19 +458,20 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
       par ^= 1u;
     }
     for (int e = beg + n; e < end; ++e) {  // neighbours beyond the slot capacity
-      const int j = a.col[e];
-      const float* row = P + (int64_t)j * a.ldp;
-      float f[CPL][4];
+      const float* row = P + (int64_t)a.col[e] * a.ldp;
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int ch = c * LPR + sub;
-        uint4 r = (ch < nchS) ? ldg_nc16(row + ch * 4) : make_uint4(0, 0, 0, 0);
-        widen(r, f[c], (const float*)nullptr);
+        if (ch < nchS) {
+          float f[4];
+          widen(ldg_nc16(row + ch * 4), f, (const float*)nullptr);
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) q[c][e2] += f[e2];
+        }
       }
-      take_neighbour<LPR, CPL, PROBLEM>(f, j > i, sub, S, xi, q, acc);
     }
-    row_epilogue<LPR, CPL, PROBLEM, TG, DO_LOSS>(a, i, sub, smask, p, q, xi, kones,
-                                                 (float)(end - beg), lam, acc);
+    if (a.xbits) store_bits<LPR, CPL>(a, i, sub, smask, p);
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, acc);
   }
   if (dead) {
     if (lane == 0 && a.err_flag) atomicOr(a.err_flag, 2);
@@ -566,11 +487,7 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
   }
   // After every warp is done with its slots, the slot area holds the block's
   // reduction scratch (block_reduce starts with a block-wide barrier).
-  float* red = reinterpret_cast<float*>(slot_area);
-  int* icnt = reinterpret_cast<int*>(slot_area + ((size_t)nwarps * S * 4 + 127) / 128 * 128);
-  unsigned long long* ham_s =
-      reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(icnt) + ((size_t)8 * S + 127) / 128 * 128);
-  block_reduce<LPR, CPL, DO_LOSS>(a, acc, red, icnt, ham_s);
+  block_reduce<LPR, CPL>(a, acc, reinterpret_cast<float*>(slot_area));
 }
 
 template <int LPR, int CPL, int PROBLEM, typename TG, bool DO_LOSS>
@@ -580,14 +497,14 @@ int launch_loss_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   int64_t want = (a.N + segs_per_block - 1) / segs_per_block;
   int grid = (int)(want < max_grid ? want : max_grid);
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)(threads / 32) * (a.S > 0 ? a.S : 1) * sizeof(float);
+  const size_t smem = DO_LOSS ? (size_t)(threads / 32) * (a.S > 0 ? a.S : 1) * sizeof(float) : 0;
   loss_kernel<LPR, CPL, PROBLEM, TG, DO_LOSS><<<grid, threads, smem, st>>>(a);
   return grid;
 }
 
 constexpr int kStagedBudget = 104 * 1024;  // dynamic shared memory per block (2 blocks / SM)
 
-template <int CPL, int PROBLEM, typename TG, bool DO_LOSS>
+template <int CPL, int PROBLEM, typename TG>
 int launch_staged_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   constexpr int threads = 256;
   constexpr int nwarps = threads / 32;
@@ -600,13 +517,12 @@ int launch_staged_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   const int rslot_bytes = (1 + CAP) * row_bytes;
   const size_t slot_area = (size_t)nwarps * RS * rslot_bytes;
   // reduction scratch aliased onto the slot area at the end
-  const size_t scratch = ((size_t)nwarps * a.S * 4 + 127) / 128 * 128 +
-                         ((size_t)8 * a.S + 127) / 128 * 128 + 8;
+  const size_t scratch = (size_t)nwarps * a.S * 4;
   if (scratch > slot_area) return -1;
   const size_t smem = bars_bytes + slot_area;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(loss_kernel_staged<CPL, PROBLEM, TG, DO_LOSS>,
+    if (cudaFuncSetAttribute(loss_kernel_staged<CPL, PROBLEM, TG>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kStagedBudget) != cudaSuccess) {
       cudaGetLastError();
@@ -617,8 +533,7 @@ int launch_staged_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   int64_t want = (a.N + nwarps - 1) / nwarps;
   int grid = (int)(want < max_grid ? want : max_grid);
   if (grid < 1) grid = 1;
-  loss_kernel_staged<CPL, PROBLEM, TG, DO_LOSS>
-      <<<grid, threads, smem, st>>>(a, RS, CAP, rslot_bytes, bars_bytes);
+  loss_kernel_staged<CPL, PROBLEM, TG><<<grid, threads, smem, st>>>(a, RS, CAP, rslot_bytes, bars_bytes);
   return grid;
 }
 
@@ -628,12 +543,14 @@ int dispatch_loss(const LossArgs& a, int nch, int max_grid, int staged_grid, cud
   if (nch <= 4) return launch_loss_t<4, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 8) return launch_loss_t<8, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 16) return launch_loss_t<16, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
-  int g = -1;
-  if (nch <= 32) g = launch_staged_t<1, PROBLEM, TG, DO_LOSS>(a, staged_grid, st);
-  else if (nch <= 64) g = launch_staged_t<2, PROBLEM, TG, DO_LOSS>(a, staged_grid, st);
-  else if (nch <= 128) g = launch_staged_t<4, PROBLEM, TG, DO_LOSS>(a, staged_grid, st);
-  else g = launch_staged_t<8, PROBLEM, TG, DO_LOSS>(a, staged_grid, st);
-  if (g > 0) return g;
+  if constexpr (DO_LOSS) {
+    int g = -1;
+    if (nch <= 32) g = launch_staged_t<1, PROBLEM, TG>(a, staged_grid, st);
+    else if (nch <= 64) g = launch_staged_t<2, PROBLEM, TG>(a, staged_grid, st);
+    else if (nch <= 128) g = launch_staged_t<4, PROBLEM, TG>(a, staged_grid, st);
+    else g = launch_staged_t<8, PROBLEM, TG>(a, staged_grid, st);
+    if (g > 0) return g;
+  }
   if (nch <= 32) return launch_loss_t<32, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 64) return launch_loss_t<32, 2, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 128) return launch_loss_t<32, 4, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
@@ -648,10 +565,9 @@ int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st) {
   // half of the usual per-SM block budget keeps every block resident.
   int staged_grid = max_grid / 2;
   if (staged_grid < 1) staged_grid = 1;
-  if (!a.do_loss) {
+  if (!a.do_loss) {  // rounding bits only: no neighbour gathers
     const int nch = (a.S + 3) / 4;
-    if (a.problem == 0) return dispatch_loss<0, float, false>(a, nch, max_grid, staged_grid, st);
-    return dispatch_loss<1, float, false>(a, nch, max_grid, staged_grid, st);
+    return dispatch_loss<0, float, false>(a, nch, max_grid, staged_grid, st);
   }
   const int nch = (int)(a.ldg / 4);
   if (a.problem == 0) {

@@ -5,9 +5,8 @@
 // a fixed budget, and latency-critical paths where an allocation (and the
 // device synchronisation it can imply) is not acceptable.  For them,
 // cpra_op_loss_noalloc takes only inputs and outputs; the per-block partial
-// sums and the integer counters of the loss kernel live in the file-scope
-// device array below, which every GPU that loads this library holds until
-// the process exits.
+// sums of the loss kernel live in the file-scope device array below, which
+// every GPU that loads this library holds until the process exits.
 //
 // Contract (also stated in cpra.h):
 //   * S <= CPRA_NOALLOC_MAX_S (1024); larger S is rejected with
@@ -17,11 +16,10 @@
 //     cudaGetSymbolAddress (once per device, under a lock); make that first
 //     call before any stream capture.
 //   * All calls on a device share the one array and it keeps the contents
-//     of the last call.  The integer counters are cleared on the caller's
-//     stream at the start of every call; the partial rows are fully written
-//     before they are read.  Calls whose work overlaps on the GPU (different
-//     streams without ordering, or concurrent host threads) race on the
-//     array and give wrong results: order them on one stream.
+//     of the last call.  Nothing in it needs clearing: every call writes
+//     each partial row it later reads.  Calls whose work overlaps on the GPU
+//     (different streams without ordering, or concurrent host threads) race
+//     on the array and give wrong results: order them on one stream.
 #include <mutex>
 
 #include "cpra.h"
@@ -32,10 +30,9 @@ namespace {
 
 constexpr int kMaxS = CPRA_NOALLOC_MAX_S;
 constexpr int kMaxBlocks = 512;
-constexpr size_t kPartialBytes = (size_t)kMaxBlocks * (((size_t)4 * kMaxS + 1 + 3) / 4 * 4) * sizeof(float);
-constexpr size_t kCounterOffset = (kPartialBytes + 255) / 256 * 256;
-constexpr size_t kCounterBytes = (2 * (size_t)kMaxS + 1) * sizeof(unsigned long long);
-constexpr size_t kScratchBytes = kCounterOffset + kCounterBytes;  // about 8.4 MB
+// per-block partial rows of 4S+1 floats (padded to a multiple of 4)
+constexpr size_t kScratchBytes =
+    (size_t)kMaxBlocks * (((size_t)4 * kMaxS + 1 + 3) / 4 * 4) * sizeof(float);  // about 8.4 MB
 
 static __device__ __align__(256) unsigned char g_loss_scratch[kScratchBytes];
 
@@ -91,11 +88,7 @@ extern "C" cpra_status cpra_op_loss_noalloc(int64_t N, int32_t S, const int32_t*
   a.grad_kind = grad_kind; a.gamma = gamma; a.nu = nu; a.G = G; a.dg = DT_F32;
   a.xbits = x_bits; a.pstride = loss_pstride(S);
   a.partials = static_cast<float*>(base);
-  a.counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(base) + kCounterOffset);
   a.do_loss = 1;
-  if (cudaMemsetAsync(a.counters, 0, (2 * (size_t)S + 1) * sizeof(unsigned long long), st) !=
-      cudaSuccess)
-    return CPRA_ECUDA;
   const int max_grid = sms * 4 < kMaxBlocks ? sms * 4 : kMaxBlocks;
   const int grid = loss_launch(a, max_grid, st);
   colsum_finalize(a.partials, grid, a.pstride, 4 * S + 1, terms, nullptr, 0, 0, nullptr, st);

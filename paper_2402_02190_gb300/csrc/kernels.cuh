@@ -55,8 +55,7 @@ struct LossArgs {
   uint32_t* xbits = nullptr;     // N x W, W = ceil(S/32)
   float* partials = nullptr;     // [grid][pstride]: cost S | pen S | ann S | psi | gsum S
   int64_t pstride = 0;
-  unsigned long long* counters = nullptr;  // obj[S], viol[S], ham  (zeroed by caller)
-  int do_loss = 1;               // 0: rounding + evaluation only
+  int do_loss = 1;               // 0: rounding bits only
   int* err_flag = nullptr;       // device word; bit 1 set if a bounded wait gave up
 };
 int64_t loss_pstride(int S);
@@ -70,6 +69,13 @@ int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st);
 void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
                      float* out, float* out2, int copy_from, int copy_n,
                      int* err_flag, cudaStream_t st);
+
+// Exact integer evaluation of rounded shots from their bits (k_eval.cu):
+// adds to counters obj[S] (MIS set size / MaxCut cut edges), viol[S] (MIS
+// edges inside the set) and counters[2S] = sum_i k_i (S - k_i).  The
+// counters must be zeroed by the caller.
+void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
+                      int problem, unsigned long long* counters, int max_grid, cudaStream_t st);
 
 // Per-shot records from the integer counters: objective, violations and the
 // FP64 qubo value; pair-Hamming total copied out.
