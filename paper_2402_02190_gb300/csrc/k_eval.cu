@@ -5,9 +5,9 @@
 // is x_is.  A segment of G >= W lanes owns one node row, lane w its word w.
 // For every edge (i, j) with j > i the lane combines x_i[w] and x_j[w]
 // (AND for MIS violations, XOR for MaxCut cut edges) and adds the 32 bits to
-// bit-sliced vertical counters (five bit planes, one ripple-carry add per
+// bit-sliced vertical counters (eight bit planes, one ripple-carry add per
 // edge); the planes are flushed to per-shot shared-memory counters before
-// they can overflow.  MIS set sizes add x_i[w] the same way; the pairwise
+// they can overflow, in practice once per thread.  MIS set sizes add x_i[w] the same way; the pairwise
 // Hamming sum adds k_i (S - k_i) with k_i = popcount of row i.  All sums are
 // integers, so the result does not depend on the order of the atomics.
 #include "common.cuh"
@@ -17,31 +17,41 @@ namespace cpra {
 
 namespace {
 
+// 32 counters of 8 bits each, stored as 8 bit planes (plane k holds bit k
+// of every counter); flushed before the 256th addition.
 struct Planes {
-  uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0;
-  int n = 0;  // additions since the last flush (< 32)
+  uint32_t p[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  int n = 0;  // additions since the last flush (< 256)
   __device__ __forceinline__ void add(uint32_t x) {
-    uint32_t t = p0 & x; p0 ^= x; x = t;
-    t = p1 & x; p1 ^= x; x = t;
-    t = p2 & x; p2 ^= x; x = t;
-    t = p3 & x; p3 ^= x; x = t;
-    p4 ^= x;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const uint32_t t = p[k] & x;
+      p[k] ^= x;
+      x = t;
+    }
+    p[7] ^= x;
     ++n;
   }
   // Adds the per-bit counts to cnt[0..31] and clears the planes.
   __device__ __forceinline__ void flush(int* cnt) {
-    if ((p0 | p1 | p2 | p3 | p4) != 0u) {
+    uint32_t any = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) any |= p[k];
+    if (any) {
 #pragma unroll 4
       for (int b = 0; b < 32; ++b) {
-        const int c = ((p0 >> b) & 1u) | (((p1 >> b) & 1u) << 1) | (((p2 >> b) & 1u) << 2) |
-                      (((p3 >> b) & 1u) << 3) | (((p4 >> b) & 1u) << 4);
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c |= (int)((p[k] >> b) & 1u) << k;
         if (c) atomicAdd(cnt + b, c);
       }
     }
-    p0 = p1 = p2 = p3 = p4 = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p[k] = 0u;
     n = 0;
   }
 };
+constexpr int kFlushAt = 255;
 
 template <int G, int PROBLEM>
 __global__ void __launch_bounds__(256)
@@ -68,35 +78,72 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
   int* cnt_viol = scnt + Wpad + 32 * sub;
   Planes obj, viol;
   long long ham = 0;
+  constexpr int U = 8;  // neighbour words loaded together
+  int beg = 0, end = 0;
+  if (first < N) {
+    beg = rowptr[first];
+    end = rowptr[first + 1];
+  }
   for (int64_t i = first; i < N; i += stride) {
+    const int64_t next = i + stride;
+    int nbeg = 0, nend = 0;
+    if (next < N) {  // next row's bounds, fetched early
+      nbeg = rowptr[next];
+      nend = rowptr[next + 1];
+    }
     const uint32_t xi = active ? bits[i * W + sub] : 0u;
+    for (int eb = beg; eb < end; eb += U) {
+      // lanes of the segment load up to U neighbour indices, then every lane
+      // loads its word of each neighbour j > i (each edge once, at its lower
+      // endpoint); all loads are in flight before any counter is updated
+      const int e = eb + (sub % U);
+      const int jl = (e < end) ? col[e] : -1;
+      const int cnt = min(U, end - eb);
+      uint32_t xs[U];
+      bool use[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = __shfl_sync(smask, jl, u % G, G);
+        use[u] = (u < cnt) && (u < G) && (j > i);
+        xs[u] = (use[u] && active) ? bits[(int64_t)j * W + sub] : 0u;
+      }
+      if (G < U) {  // segments narrower than U lanes: the rest one index at a time
+        for (int u = G; u < cnt; ++u) {
+          const int j = col[eb + u];
+          if (j > i) {
+            const uint32_t xj = active ? bits[(int64_t)j * W + sub] : 0u;
+            if (PROBLEM == 0) {
+              viol.add(xi & xj);
+              if (viol.n == kFlushAt) viol.flush(cnt_viol);
+            } else {
+              obj.add(xi ^ xj);
+              if (obj.n == kFlushAt) obj.flush(cnt_obj);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!use[u]) continue;
+        if (PROBLEM == 0) {
+          viol.add(xi & xs[u]);
+          if (viol.n == kFlushAt) viol.flush(cnt_viol);
+        } else {
+          obj.add(xi ^ xs[u]);
+          if (obj.n == kFlushAt) obj.flush(cnt_obj);
+        }
+      }
+    }
     int k = __popc(xi);
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) k += __shfl_xor_sync(smask, k, off);
     if (sub == 0) ham += (long long)k * (long long)(S - k);
     if (PROBLEM == 0) {
       obj.add(xi);
-      if (obj.n == 31) obj.flush(cnt_obj);
+      if (obj.n == kFlushAt) obj.flush(cnt_obj);
     }
-    const int beg = rowptr[i];
-    const int end = rowptr[i + 1];
-    for (int eb = beg; eb < end; eb += G) {
-      const int e = eb + sub;
-      const int jl = (e < end) ? col[e] : -1;
-      const int cnt = min(G, end - eb);
-      for (int t = 0; t < cnt; ++t) {
-        const int j = __shfl_sync(smask, jl, t, G);
-        if (j <= i) continue;  // each edge once, at its lower endpoint
-        const uint32_t xj = active ? bits[(int64_t)j * W + sub] : 0u;
-        if (PROBLEM == 0) {
-          viol.add(xi & xj);
-          if (viol.n == 31) viol.flush(cnt_viol);
-        } else {
-          obj.add(xi ^ xj);
-          if (obj.n == 31) obj.flush(cnt_obj);
-        }
-      }
-    }
+    beg = nbeg;
+    end = nend;
   }
   if (active) {
     obj.flush(cnt_obj);
