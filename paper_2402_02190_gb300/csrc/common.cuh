@@ -93,6 +93,50 @@ __device__ __forceinline__ void storeN(bf16* p, const float* v) {
   }
 }
 
+// L2 eviction hints for data touched once (streamed outputs and row reads):
+// marking them evict-first keeps the gathered operand resident in L2 longer.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Coherent 16-byte load (the data may be rewritten later by the same kernel).
+__device__ __forceinline__ uint4 ld_stream16(const void* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_stream16(void* p, const uint4& v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+// storeN for N a multiple of 4 (float) or 8 (bf16), with the L2 hint.
+template <int N>
+__device__ __forceinline__ void storeN_stream(float* p, const float* v, uint64_t pol) {
+#pragma unroll
+  for (int k = 0; k < N; k += 4)
+    st_stream16(p + k, make_uint4(__float_as_uint(v[k]), __float_as_uint(v[k + 1]),
+                                  __float_as_uint(v[k + 2]), __float_as_uint(v[k + 3])),
+                pol);
+}
+template <int N>
+__device__ __forceinline__ void storeN_stream(bf16* p, const float* v, uint64_t pol) {
+  static_assert(N % 8 == 0, "bf16 streamed stores move 8 elements");
+#pragma unroll
+  for (int k = 0; k < N; k += 8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[k + 2 * q], v[k + 2 * q + 1]);
+      w[q] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    st_stream16(p + k, make_uint4(w[0], w[1], w[2], w[3]), pol);
+  }
+}
+
 // Sum over the lanes of an aligned power-of-two segment of width W.
 template <int W>
 __device__ __forceinline__ float seg_sum(float v, unsigned mask) {

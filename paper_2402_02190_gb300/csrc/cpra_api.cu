@@ -382,8 +382,8 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
     SpmmArgs a;
     a.N = N; a.H = H0; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
     a.X = c->XM; a.ldx = 2 * H0; a.Y = act_off(c->XM, H0, c); a.ldy = 2 * H0; a.mean = 1;
-    a.dx = c->act_dt; a.dy = c->act_dt;
-    spmm_launch(a, max_grid, c->stream);
+    a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
+    if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
     c->launches += 1;
   }
   {  // H1 = relu([X0|M1] Wcat1^T + b1)
@@ -403,8 +403,8 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
     SpmmArgs a;
     a.N = N; a.H = H1; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
     a.X = c->HM; a.ldx = 2 * H1; a.Y = act_off(c->HM, H1, c); a.ldy = 2 * H1; a.mean = 1;
-    a.dx = c->act_dt; a.dy = c->act_dt;
-    spmm_launch(a, max_grid, c->stream);
+    a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
+    if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
     c->launches += 1;
   }
   {  // P = sigmoid([H1|M2] Wcat2^T + b2)
@@ -482,9 +482,10 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
     a.add = c->GHM; a.ldadd = 2 * H1;
     a.mask = c->HM; a.ldm = 2 * H1;
     a.Y = c->GHM; a.ldy = 2 * H1; a.mean = 0;
-    a.dx = c->act_dt; a.dy = c->act_dt;
+    a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     a.colsum_partials = c->colsum_part;
-    const int grid = spmm_launch(a, std::min(max_grid, kLossMaxGrid), c->stream);
+    const int grid = spmm_launch(a, c->num_sms, std::min(max_grid, kLossMaxGrid), c->stream);
+    if (grid < 0) return CPRA_EINVAL;
     colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
                     c->stream);
     c->launches += 2;
@@ -518,8 +519,8 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
       a.X = act_off(c->GXM, H0, c); a.ldx = 2 * H0;
       a.add = c->GXM; a.ldadd = 2 * H0;
       a.Y = c->gX0; a.ldy = H0; a.mean = 0;
-      a.dx = c->act_dt; a.dy = DT_F32;
-      spmm_launch(a, max_grid, c->stream);
+      a.dx = c->act_dt; a.dy = DT_F32; a.err_flag = c->err_flag;
+      if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
       c->launches += 1;
     }
   }

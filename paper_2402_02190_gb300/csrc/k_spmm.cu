@@ -2,15 +2,35 @@
 // adjoint.  One power-of-two segment of LPR lanes owns one node row; each lane
 // moves 16-byte vectors, CPL of them per row.  Neighbour rows are gathered
 // four at a time so that every lane keeps 4*CPL independent 16-byte loads in
-// flight.
+// flight.  Everything but the gathered operand is touched once, so those
+// reads and the output rows carry an L2 evict-first hint: the gathered rows
+// then stay in L2 longer and fewer of the repeated gathers reach HBM.
+//
+// The operand set of a launch is a template parameter (KIND), so the forward
+// aggregation carries no add/mask/column-sum code and fits in fewer
+// registers; the grid is the number of blocks that are resident at once.
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace cpra {
 
-template <typename TX, typename TY, int LPR, int CPL>
-__global__ void __launch_bounds__(256)
+namespace {
+
+enum SpmmKind {
+  KIND_MEAN = 0,             // Y = D^-1 A X                     (forward aggregation)
+  KIND_ADD_MASK_COLSUM = 1,  // Y = (add + A X) * 1[mask > 0], column sums of Y
+  KIND_ADD = 2,              // Y = add + A X
+};
+
+template <typename TX, typename TY, int LPR, int CPL, int KIND>
+__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_ADD_MASK_COLSUM ? 4 : 5))
 spmm_rows_kernel(SpmmArgs a) {
+  constexpr bool MEAN = KIND == KIND_MEAN;
+  constexpr bool HAS_ADD = KIND != KIND_MEAN;
+  constexpr bool HAS_MASK = KIND == KIND_ADD_MASK_COLSUM;
+  constexpr bool COLSUM = KIND == KIND_ADD_MASK_COLSUM;
   constexpr int VEC = V16<TX>::n;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LPR - 1);
@@ -22,9 +42,10 @@ spmm_rows_kernel(SpmmArgs a) {
   const int64_t stride = (int64_t)gridDim.x * segs_per_block;
   const int nchunks = a.H / VEC;
   const TX* __restrict__ X = static_cast<const TX*>(a.X);
-  TY* __restrict__ Y = static_cast<TY*>(a.Y);
-  const TX* __restrict__ ADD = static_cast<const TX*>(a.add);
+  TY* Y = static_cast<TY*>(a.Y);
+  const TX* ADD = static_cast<const TX*>(a.add);  // may alias Y (same row, read first)
   const TX* __restrict__ MASK = static_cast<const TX*>(a.mask);
+  const uint64_t pol = l2_evict_first_policy();
 
   float csum[CPL][VEC];
 #pragma unroll
@@ -33,6 +54,17 @@ spmm_rows_kernel(SpmmArgs a) {
     for (int v = 0; v < VEC; ++v) csum[c][v] = 0.f;
 
   for (int64_t i = first; i < a.N; i += stride) {
+    // the row's own operands first, so that they arrive with the gathers
+    uint4 rad[CPL], rmk[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int ch = c * LPR + sub;
+      rad[c] = rmk[c] = make_uint4(0, 0, 0, 0);
+      if (ch < nchunks) {
+        if constexpr (HAS_ADD) rad[c] = ld_stream16(ADD + i * a.ldadd + ch * VEC, pol);
+        if constexpr (HAS_MASK) rmk[c] = ld_stream16(MASK + i * a.ldm + ch * VEC, pol);
+      }
+    }
     float acc[CPL][VEC];
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
@@ -84,7 +116,8 @@ spmm_rows_kernel(SpmmArgs a) {
       }
     }
 
-    const float s = a.mean ? a.inv_deg[i] : 1.f;
+    float s = 1.f;
+    if constexpr (MEAN) s = a.inv_deg[i];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       const int ch = c * LPR + sub;
@@ -92,88 +125,126 @@ spmm_rows_kernel(SpmmArgs a) {
       float o[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; ++v) o[v] = acc[c][v];
-      if (ADD) {
+      if constexpr (HAS_ADD) {
         float ad[VEC];
-        load16(ADD + i * a.ldadd + ch * VEC, ad);
+        widen(rad[c], ad, (const TX*)nullptr);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] += ad[v];
       }
+      if constexpr (MEAN) {
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) o[v] *= s;
-      if (MASK) {
+        for (int v = 0; v < VEC; ++v) o[v] *= s;
+      }
+      if constexpr (HAS_MASK) {
         float mk[VEC];
-        load16(MASK + i * a.ldm + ch * VEC, mk);
+        widen(rmk[c], mk, (const TX*)nullptr);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = (mk[v] > 0.f) ? o[v] : 0.f;
       }
+      if constexpr (COLSUM) {
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) csum[c][v] += o[v];
-      storeN<VEC>(Y + i * a.ldy + ch * VEC, o);
+        for (int v = 0; v < VEC; ++v) csum[c][v] += o[v];
+      }
+      storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
     }
   }
 
-  if (a.colsum_partials == nullptr) return;
-  // Fixed-order block reduction of the per-lane column sums.
-  __syncwarp();
+  if constexpr (COLSUM) {
+    // Fixed-order block reduction of the per-lane column sums.
+    __syncwarp();
 #pragma unroll
-  for (int c = 0; c < CPL; ++c)
+    for (int c = 0; c < CPL; ++c)
 #pragma unroll
-    for (int v = 0; v < VEC; ++v)
+      for (int v = 0; v < VEC; ++v)
 #pragma unroll
-      for (int off = LPR; off < 32; off <<= 1)
-        csum[c][v] += __shfl_xor_sync(0xffffffffu, csum[c][v], off);
-  extern __shared__ float red[];  // [warps][H]
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  if (lane < LPR) {
+        for (int off = LPR; off < 32; off <<= 1)
+          csum[c][v] += __shfl_xor_sync(0xffffffffu, csum[c][v], off);
+    extern __shared__ float red[];  // [warps][H]
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    if (lane < LPR) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int ch = c * LPR + sub;
-      if (ch < nchunks)
+      for (int c = 0; c < CPL; ++c) {
+        const int ch = c * LPR + sub;
+        if (ch < nchunks)
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) red[warp * a.H + ch * VEC + v] = csum[c][v];
+          for (int v = 0; v < VEC; ++v) red[warp * a.H + ch * VEC + v] = csum[c][v];
+      }
     }
-  }
-  __syncthreads();
-  for (int col = threadIdx.x; col < a.H; col += blockDim.x) {
-    float t = 0.f;
-    for (int w = 0; w < nwarps; ++w) t += red[w * a.H + col];
-    a.colsum_partials[(int64_t)blockIdx.x * a.H + col] = t;
+    __syncthreads();
+    for (int col = threadIdx.x; col < a.H; col += blockDim.x) {
+      float t = 0.f;
+      for (int w = 0; w < nwarps; ++w) t += red[w * a.H + col];
+      a.colsum_partials[(int64_t)blockIdx.x * a.H + col] = t;
+    }
   }
 }
 
-template <typename TX, typename TY, int LPR, int CPL>
-static int launch_t(const SpmmArgs& a, int max_grid, cudaStream_t st) {
+// Resident blocks per SM for one kernel and dynamic shared size; `cache`
+// (one per kernel instantiation) keeps the last answer as (smem << 8) | blocks.
+template <typename K>
+int resident_blocks(K kernel, int threads, size_t smem, std::atomic<long long>& cache) {
+  const long long c = cache.load(std::memory_order_relaxed);
+  if (c >= 0 && (size_t)(c >> 8) == smem) return (int)(c & 0xff);
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem) != cudaSuccess ||
+      blocks < 1) {
+    cudaGetLastError();
+    blocks = 1;
+  }
+  if (blocks > 255) blocks = 255;
+  cache.store(((long long)smem << 8) | blocks, std::memory_order_relaxed);
+  return blocks;
+}
+
+template <typename TX, typename TY, int LPR, int CPL, int KIND>
+int launch_t(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   constexpr int threads = 256;
   const int segs_per_block = (threads / 32) * (32 / LPR);
-  int64_t want = (a.N + segs_per_block - 1) / segs_per_block;
-  int grid = (int)(want < max_grid ? want : max_grid);
+  const size_t smem = (KIND == KIND_ADD_MASK_COLSUM) ? (size_t)(threads / 32) * a.H * sizeof(float) : 0;
+  auto kernel = spmm_rows_kernel<TX, TY, LPR, CPL, KIND>;
+  static std::atomic<long long> occ_cache{-1};
+  const int64_t resident = (int64_t)resident_blocks(kernel, threads, smem, occ_cache) * num_sms;
+  int64_t grid = (a.N + segs_per_block - 1) / segs_per_block;
+  if (grid > resident) grid = resident;
+  if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
-  const size_t smem = a.colsum_partials ? (size_t)(threads / 32) * a.H * sizeof(float) : 0;
-  spmm_rows_kernel<TX, TY, LPR, CPL><<<grid, threads, smem, st>>>(a);
-  return grid;
+  kernel<<<(int)grid, threads, smem, st>>>(a);
+  return (int)grid;
 }
 
-template <typename TX, typename TY>
-static int dispatch_lpr(const SpmmArgs& a, int max_grid, cudaStream_t st) {
+template <typename TX, typename TY, int KIND>
+int dispatch_lpr(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   const int nch = a.H / V16<TX>::n;
-  if (nch <= 2) return launch_t<TX, TY, 2, 1>(a, max_grid, st);
-  if (nch <= 4) return launch_t<TX, TY, 4, 1>(a, max_grid, st);
-  if (nch <= 8) return launch_t<TX, TY, 8, 1>(a, max_grid, st);
-  if (nch <= 16) return launch_t<TX, TY, 16, 1>(a, max_grid, st);
-  if (nch <= 32) return launch_t<TX, TY, 32, 1>(a, max_grid, st);
-  if (nch <= 64) return launch_t<TX, TY, 32, 2>(a, max_grid, st);
-  if (nch <= 128) return launch_t<TX, TY, 32, 4>(a, max_grid, st);
-  return launch_t<TX, TY, 32, 8>(a, max_grid, st);
+  if (nch <= 2) return launch_t<TX, TY, 2, 1, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 4) return launch_t<TX, TY, 4, 1, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 8) return launch_t<TX, TY, 8, 1, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 16) return launch_t<TX, TY, 16, 1, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 32) return launch_t<TX, TY, 32, 1, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 64) return launch_t<TX, TY, 32, 2, KIND>(a, num_sms, max_grid, st);
+  if (nch <= 128) return launch_t<TX, TY, 32, 4, KIND>(a, num_sms, max_grid, st);
+  return launch_t<TX, TY, 32, 8, KIND>(a, num_sms, max_grid, st);
 }
 
-int spmm_launch(const SpmmArgs& a, int max_grid, cudaStream_t st) {
-  if (a.dx == DT_BF16) {
-    if (a.dy == DT_BF16) return dispatch_lpr<bf16, bf16>(a, max_grid, st);
-    return dispatch_lpr<bf16, float>(a, max_grid, st);
+}  // namespace
+
+int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
+  const bool add = a.add != nullptr, mask = a.mask != nullptr, cs = a.colsum_partials != nullptr;
+  const bool same = a.dx == a.dy;
+  if (a.mean && !add && !mask && !cs && same) {
+    return a.dx == DT_BF16 ? dispatch_lpr<bf16, bf16, KIND_MEAN>(a, num_sms, max_grid, st)
+                           : dispatch_lpr<float, float, KIND_MEAN>(a, num_sms, max_grid, st);
   }
-  if (a.dy == DT_BF16) return dispatch_lpr<float, bf16>(a, max_grid, st);
-  return dispatch_lpr<float, float>(a, max_grid, st);
+  if (!a.mean && add && mask && cs && same) {
+    return a.dx == DT_BF16
+               ? dispatch_lpr<bf16, bf16, KIND_ADD_MASK_COLSUM>(a, num_sms, max_grid, st)
+               : dispatch_lpr<float, float, KIND_ADD_MASK_COLSUM>(a, num_sms, max_grid, st);
+  }
+  if (!a.mean && add && !mask && !cs && a.dy == DT_F32) {
+    return a.dx == DT_BF16 ? dispatch_lpr<bf16, float, KIND_ADD>(a, num_sms, max_grid, st)
+                           : dispatch_lpr<float, float, KIND_ADD>(a, num_sms, max_grid, st);
+  }
+  return -1;  // operand set not used by the training step
 }
 
 }  // namespace cpra

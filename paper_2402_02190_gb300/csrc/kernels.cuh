@@ -34,9 +34,15 @@ struct SpmmArgs {
   float* colsum_partials = nullptr;
   int dx = DT_F32;
   int dy = DT_F32;
+  int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
 };
-// Returns the grid size used (the row count of colsum_partials).
-int spmm_launch(const SpmmArgs& a, int max_grid, cudaStream_t st);
+// Three operand sets are supported (the ones the training step uses):
+// mean aggregation (no add/mask/colsum, dy == dx), add + mask + colsum with
+// mean = 0 (dy == dx), and add only with mean = 0 (dy = f32).  The grid is the
+// number of blocks resident at once on num_sms SMs, at most max_grid.
+// Returns the grid size used (the row count of colsum_partials), or -1 for
+// an operand set outside these three (nothing is launched).
+int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st);
 
 // ---------------------------------------------------------------- loss
 // Fused SpMM + relaxed loss + rounding/evaluation (see cpra_op_loss).
