@@ -70,7 +70,11 @@ typedef struct cpra_config {
   int32_t recompute;        /* 1: layer-1 activations are recomputed in backward  */
   int32_t train_embedding;  /* 1: node embeddings h^0 are trained (default)       */
   int32_t diversity_kind;   /* CPRA_DIV_STD (Eq. ...-variation) or CPRA_DIV_VAR   */
-  int32_t reserved0;
+  int32_t keep_emb_grad;    /* 0 (default): cpra_step fuses the embedding Adam
+                               step into the last backward aggregation and does
+                               not store dR/dh^0; 1: it also stores dR/dh^0
+                               (CPRA_T_EMB_GRAD), 512 MB more HBM traffic per
+                               10^6 x 128 embedding                             */
   const float* lambda;      /* host [S], penalty lambda_s per shot (MIS); copied
                                at init; may be NULL for MaxCut                     */
   float nu;                 /* diversity weight (0 disables Psi)                  */
@@ -94,8 +98,9 @@ typedef struct cpra_shot_eval {
 typedef struct cpra_ctx cpra_ctx;
 
 /* Fills *cfg with defaults: MIS, S = 8, H0 = H1 = 16, alpha = 2, FP32,
-   recompute 0, train_embedding 1, DIV_STD, nu = 0, gamma -2 -> 0.1 over 3000
-   steps, Adam lr 1e-3, betas (0.9, 0.999), eps 1e-8, wd 0, seed 1. */
+   recompute 0, train_embedding 1, keep_emb_grad 0, DIV_STD, nu = 0,
+   gamma -2 -> 0.1 over 3000 steps, Adam lr 1e-3, betas (0.9, 0.999),
+   eps 1e-8, wd 0, seed 1. */
 CPRA_API void cpra_config_default(cpra_config* cfg);
 
 /* Number of trainable GNN parameters excluding node embeddings:
@@ -176,7 +181,8 @@ enum {
   CPRA_T_EMB_M = 4,     /* float [N x H0]                                     */
   CPRA_T_EMB_V = 5,     /* float [N x H0]                                     */
   CPRA_T_GRAD = 6,      /* float [param_count] dR/dtheta of the last step     */
-  CPRA_T_EMB_GRAD = 7,  /* float [N x H0] dR/dh^0 of the last step            */
+  CPRA_T_EMB_GRAD = 7,  /* float [N x H0] dR/dh^0 of the last cpra_step with
+                           keep_emb_grad = 1 (or of the last cpra_backward)  */
   CPRA_T_P = 8,         /* float [N x S] P of the last forward                */
   CPRA_T_GZ2 = 9,       /* float [N x S] dR/dZ2 of the last step (upcast)     */
   CPRA_T_STEP = 10,     /* int64 [1] Adam step counter                        */

@@ -48,7 +48,7 @@ class Config(C.Structure):
     _fields_ = [
         ("problem", C.c_int32), ("S", C.c_int32), ("H0", C.c_int32), ("H1", C.c_int32),
         ("alpha", C.c_int32), ("precision", C.c_int32), ("recompute", C.c_int32),
-        ("train_embedding", C.c_int32), ("diversity_kind", C.c_int32), ("reserved0", C.c_int32),
+        ("train_embedding", C.c_int32), ("diversity_kind", C.c_int32), ("keep_emb_grad", C.c_int32),
         ("lambda_", C.POINTER(C.c_float)), ("nu", C.c_float), ("gamma0", C.c_float),
         ("gamma1", C.c_float), ("schedule_steps", C.c_int64), ("lr", C.c_float),
         ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),

@@ -137,6 +137,22 @@ __device__ __forceinline__ void storeN_stream(bf16* p, const float* v, uint64_t 
   }
 }
 
+// One Adam step (Kingma & Ba) on one parameter with optional decoupled
+// weight decay (AdamW), the optimiser of the Experiments section; the bias
+// corrections bc1 = 1 - beta1^t and bc2 = 1 - beta2^t come from the host.
+// Shared by the parameter update and the fused embedding update so that both
+// round identically.
+__device__ __forceinline__ float adam_update(float th, float& m, float& v, float g, float lr,
+                                             float b1, float b2, float eps, float wd, float bc1,
+                                             float bc2) {
+  if (wd != 0.f) th = th * (1.f - lr * wd);
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  const float mhat = m / bc1;
+  const float vhat = v / bc2;
+  return th - lr * mhat / (sqrtf(vhat) + eps);
+}
+
 // Sum over the lanes of an aligned power-of-two segment of width W.
 template <int W>
 __device__ __forceinline__ float seg_sum(float v, unsigned mask) {

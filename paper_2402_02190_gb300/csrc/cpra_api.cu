@@ -49,7 +49,7 @@ enum KernelId {
 const char* kKernelNames[K_COUNT_] = {
     "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
     "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
-    "gemm_dgrad1", "spmm_bwd1",   "adam",       "adam_embedding", "round_eval"};
+    "gemm_dgrad1", "spmm_bwd1",   "adam",       "spmm_bwd1_adam_embedding", "round_eval"};
 
 constexpr size_t kAlign = 256;
 
@@ -181,6 +181,7 @@ std::string validate_config(const cpra_config* cfg) {
   if (cfg->alpha < 2 || cfg->alpha > 32 || cfg->alpha % 2) return "alpha must be even, 2..32";
   if (cfg->precision != CPRA_FP32 && cfg->precision != CPRA_BF16) return "precision must be FP32 or BF16";
   if (cfg->diversity_kind != CPRA_DIV_STD && cfg->diversity_kind != CPRA_DIV_VAR) return "bad diversity_kind";
+  if (cfg->keep_emb_grad != 0 && cfg->keep_emb_grad != 1) return "keep_emb_grad must be 0 or 1";
   if (cfg->problem == CPRA_MIS && cfg->lambda == nullptr) return "MIS needs lambda[S]";
   if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
   if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
@@ -453,9 +454,17 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
   return CPRA_OK;
 }
 
+// Adam bias corrections for the next optimiser step t = opt_steps + 1.
+void adam_bias(const cpra_ctx* c, float* bc1, float* bc2) {
+  const double t = (double)(c->opt_steps + 1);
+  *bc1 = (float)(1.0 - std::pow((double)c->cfg.beta1, t));
+  *bc2 = (float)(1.0 - std::pow((double)c->cfg.beta2, t));
+}
+
 // Adjoint of the last forward: dR/dtheta into c->grad and, with emb_grad,
-// dR/dh^0 into c->gX0.
-cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
+// dR/dh^0 into c->gX0.  With fuse_adam the last aggregation also takes the
+// Adam step on the embeddings (and stores dR/dh^0 only when keep_emb_grad).
+cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
   const int64_t N = c->N;
   const int H0 = c->H0, H1 = c->H1;
   const int max_grid = c->num_sms * 8;
@@ -512,13 +521,22 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
       g.row_scale = c->inv_deg; g.n_valid = 2 * H0;
       dense(c, g);
     }
-    {  // dX0 = G_X0a + sum_j G_M1_j/deg_j
-      Region r(c, K_SPMM_BWD1);
+    {  // dX0 = G_X0a + sum_j G_M1_j/deg_j  [then Adam on h^0]
+      Region r(c, fuse_adam ? K_ADAM_EMB : K_SPMM_BWD1);
       SpmmArgs a;
       a.N = N; a.H = H0; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
       a.X = act_off(c->GXM, H0, c); a.ldx = 2 * H0;
       a.add = c->GXM; a.ldadd = 2 * H0;
       a.Y = c->gX0; a.ldy = H0; a.mean = 0;
+      if (fuse_adam) {
+        a.adam = 1;
+        if (!c->cfg.keep_emb_grad) a.Y = nullptr;
+        a.emb = c->X0m; a.emb_m = c->X0_m; a.emb_v = c->X0_v;
+        a.shadow = c->XM; a.lds = 2 * H0;
+        a.lr = c->cfg.lr; a.beta1 = c->cfg.beta1; a.beta2 = c->cfg.beta2;
+        a.eps = c->cfg.eps; a.wd = c->cfg.weight_decay;
+        adam_bias(c, &a.bc1, &a.bc2);
+      }
       a.dx = c->act_dt; a.dy = DT_F32; a.err_flag = c->err_flag;
       if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
       c->launches += 1;
@@ -527,26 +545,17 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad) {
   return CPRA_OK;
 }
 
-// Adam on theta (+ BF16 shadows) and, when trained, on the embeddings.
+// Adam on theta (+ BF16 shadows); the embeddings take their Adam step inside
+// the last backward aggregation (run_backward with fuse_adam).
 cpra_status run_update(cpra_ctx* c) {
-  const int64_t N = c->N;
-  const int H0 = c->H0;
-  const int64_t t = c->opt_steps + 1;
-  const float bc1 = (float)(1.0 - std::pow((double)c->cfg.beta1, (double)t));
-  const float bc2 = (float)(1.0 - std::pow((double)c->cfg.beta2, (double)t));
+  float bc1, bc2;
+  adam_bias(c, &bc1, &bc2);
   {
     Region r(c, K_ADAM);
     adam_launch(c->nparam, c->theta, c->theta_m, c->theta_v, c->grad, c->cfg.lr, c->cfg.beta1,
                 c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, c->stream);
     c->launches += 1;
     refresh_shadows(c);
-  }
-  if (c->cfg.train_embedding) {
-    Region r(c, K_ADAM_EMB);
-    adam_emb_launch(N, H0, c->X0m, c->X0_m, c->X0_v, c->gX0, c->cfg.lr, c->cfg.beta1,
-                    c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, c->XM, 2 * H0,
-                    c->act_dt, c->stream);
-    c->launches += 1;
   }
   c->opt_steps += 1;
   return CPRA_OK;
@@ -584,6 +593,7 @@ void cpra_config_default(cpra_config* cfg) {
   cfg->precision = CPRA_FP32;
   cfg->recompute = 0;
   cfg->train_embedding = 1;
+  cfg->keep_emb_grad = 0;
   cfg->diversity_kind = CPRA_DIV_STD;
   cfg->lambda = nullptr;
   cfg->nu = 0.f;
@@ -730,7 +740,8 @@ cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
   const float gamma = gamma_at(c->cfg, t);
   cpra_status s = run_forward_and_loss(c, gamma, true);
   if (s != CPRA_OK) return s;
-  s = run_backward(c, c->cfg.train_embedding != 0);
+  const bool emb = c->cfg.train_embedding != 0;
+  s = run_backward(c, emb, /*fuse_adam=*/emb);
   if (s != CPRA_OK) return s;
   s = run_update(c);
   if (s != CPRA_OK) return s;

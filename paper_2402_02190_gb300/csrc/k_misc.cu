@@ -8,48 +8,15 @@ namespace cpra {
 
 namespace {
 
-// Adam (Kingma & Ba) with optional decoupled weight decay (AdamW), the
-// optimiser of the Experiments section; bias corrections bc1 = 1 - beta1^t,
-// bc2 = 1 - beta2^t come from the host.
-__device__ __forceinline__ float adam_one(float th, float& m, float& v, float g, float lr,
-                                          float b1, float b2, float eps, float wd, float bc1,
-                                          float bc2) {
-  if (wd != 0.f) th = th * (1.f - lr * wd);
-  m = b1 * m + (1.f - b1) * g;
-  v = b2 * v + (1.f - b2) * g * g;
-  const float mhat = m / bc1;
-  const float vhat = v / bc2;
-  return th - lr * mhat / (sqrtf(vhat) + eps);
-}
-
 __global__ void adam_kernel(int64_t n, float* __restrict__ th, float* __restrict__ m,
                             float* __restrict__ v, const float* __restrict__ g, float lr,
                             float b1, float b2, float eps, float wd, float bc1, float bc2) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float mi = m[i], vi = v[i];
-    th[i] = adam_one(th[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
+    th[i] = adam_update(th[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
     m[i] = mi;
     v[i] = vi;
-  }
-}
-
-template <typename TS>
-__global__ void adam_emb_kernel(int64_t N, int H0, float* __restrict__ X0,
-                                float* __restrict__ m, float* __restrict__ v,
-                                const float* __restrict__ g, float lr, float b1, float b2,
-                                float eps, float wd, float bc1, float bc2, TS* shadow,
-                                int64_t lds) {
-  const int64_t total = N * H0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float mi = m[i], vi = v[i];
-    const float x = adam_one(X0[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
-    X0[i] = x;
-    m[i] = mi;
-    v[i] = vi;
-    const int64_t r = i / H0, c = i % H0;
-    shadow[r * lds + c] = from_f<TS>(x);
   }
 }
 
@@ -166,18 +133,6 @@ void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g, fl
                  cudaStream_t st) {
   adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, m, v, g, lr, beta1, beta2, eps, wd, bc1,
                                            bc2);
-}
-
-void adam_emb_launch(int64_t N, int H0, float* X0, float* m, float* v, const float* g,
-                     float lr, float beta1, float beta2, float eps, float wd, float bc1,
-                     float bc2, void* shadow, int64_t lds, int dsh, cudaStream_t st) {
-  const unsigned grid = grid_for(N * H0);
-  if (dsh == DT_BF16)
-    adam_emb_kernel<bf16><<<grid, 256, 0, st>>>(N, H0, X0, m, v, g, lr, beta1, beta2, eps, wd,
-                                                bc1, bc2, static_cast<bf16*>(shadow), lds);
-  else
-    adam_emb_kernel<float><<<grid, 256, 0, st>>>(N, H0, X0, m, v, g, lr, beta1, beta2, eps, wd,
-                                                 bc1, bc2, static_cast<float*>(shadow), lds);
 }
 
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd, int ddst,

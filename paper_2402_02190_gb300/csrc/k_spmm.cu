@@ -22,15 +22,17 @@ enum SpmmKind {
   KIND_MEAN = 0,             // Y = D^-1 A X                     (forward aggregation)
   KIND_ADD_MASK_COLSUM = 1,  // Y = (add + A X) * 1[mask > 0], column sums of Y
   KIND_ADD = 2,              // Y = add + A X
+  KIND_ADD_ADAM = 3,         // g = add + A X; Adam step on the embedding row with g
 };
 
 template <typename TX, typename TY, int LPR, int CPL, int KIND>
-__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_ADD_MASK_COLSUM ? 4 : 5))
+__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_MEAN || KIND == KIND_ADD ? 5 : 4))
 spmm_rows_kernel(SpmmArgs a) {
   constexpr bool MEAN = KIND == KIND_MEAN;
   constexpr bool HAS_ADD = KIND != KIND_MEAN;
   constexpr bool HAS_MASK = KIND == KIND_ADD_MASK_COLSUM;
   constexpr bool COLSUM = KIND == KIND_ADD_MASK_COLSUM;
+  constexpr bool ADAM = KIND == KIND_ADD_ADAM;
   constexpr int VEC = V16<TX>::n;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LPR - 1);
@@ -145,7 +147,29 @@ spmm_rows_kernel(SpmmArgs a) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) csum[c][v] += o[v];
       }
-      storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
+      if constexpr (ADAM) {
+        // o is dR/dh^0 for this chunk: one Adam step on the FP32 master row,
+        // its moments, and the activation-dtype copy the forward reads
+        const int64_t off = i * a.H + ch * VEC;
+        float th[VEC], m[VEC], vv[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; q += 4) {
+          widen(ld_stream16(a.emb + off + q, pol), th + q, (const float*)nullptr);
+          widen(ld_stream16(a.emb_m + off + q, pol), m + q, (const float*)nullptr);
+          widen(ld_stream16(a.emb_v + off + q, pol), vv + q, (const float*)nullptr);
+        }
+        if (Y) storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          th[v] = adam_update(th[v], m[v], vv[v], o[v], a.lr, a.beta1, a.beta2, a.eps, a.wd,
+                              a.bc1, a.bc2);
+        storeN_stream<VEC>(a.emb + off, th, pol);
+        storeN_stream<VEC>(a.emb_m + off, m, pol);
+        storeN_stream<VEC>(a.emb_v + off, vv, pol);
+        storeN_stream<VEC>(static_cast<TX*>(a.shadow) + i * a.lds + ch * VEC, th, pol);
+      } else {
+        storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
+      }
     }
   }
 
@@ -231,6 +255,7 @@ int dispatch_lpr(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) 
 int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   const bool add = a.add != nullptr, mask = a.mask != nullptr, cs = a.colsum_partials != nullptr;
   const bool same = a.dx == a.dy;
+  if (a.adam && (a.mean || !add || mask || cs)) return -1;
   if (a.mean && !add && !mask && !cs && same) {
     return a.dx == DT_BF16 ? dispatch_lpr<bf16, bf16, KIND_MEAN>(a, num_sms, max_grid, st)
                            : dispatch_lpr<float, float, KIND_MEAN>(a, num_sms, max_grid, st);
@@ -239,6 +264,11 @@ int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
     return a.dx == DT_BF16
                ? dispatch_lpr<bf16, bf16, KIND_ADD_MASK_COLSUM>(a, num_sms, max_grid, st)
                : dispatch_lpr<float, float, KIND_ADD_MASK_COLSUM>(a, num_sms, max_grid, st);
+  }
+  if (!a.mean && add && !mask && !cs && a.dy == DT_F32 && a.adam) {
+    if (!a.emb || !a.emb_m || !a.emb_v || !a.shadow) return -1;
+    return a.dx == DT_BF16 ? dispatch_lpr<bf16, float, KIND_ADD_ADAM>(a, num_sms, max_grid, st)
+                           : dispatch_lpr<float, float, KIND_ADD_ADAM>(a, num_sms, max_grid, st);
   }
   if (!a.mean && add && !mask && !cs && a.dy == DT_F32) {
     return a.dx == DT_BF16 ? dispatch_lpr<bf16, float, KIND_ADD>(a, num_sms, max_grid, st)

@@ -35,10 +35,22 @@ struct SpmmArgs {
   int dx = DT_F32;
   int dy = DT_F32;
   int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
+  // Fused embedding update (adam = 1, with add, mean = 0, dy = f32): the row
+  // result g_i is the embedding gradient; Adam updates emb/emb_m/emb_v
+  // ([N x H] f32, row stride H) and writes the updated row to shadow (dtype
+  // dx, row stride lds).  Y may be null (the gradient is then not stored).
+  int adam = 0;
+  float* emb = nullptr;
+  float* emb_m = nullptr;
+  float* emb_v = nullptr;
+  void* shadow = nullptr;
+  int64_t lds = 0;
+  float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
 };
-// Three operand sets are supported (the ones the training step uses):
+// Four operand sets are supported (the ones the training step uses):
 // mean aggregation (no add/mask/colsum, dy == dx), add + mask + colsum with
-// mean = 0 (dy == dx), and add only with mean = 0 (dy = f32).  The grid is the
+// mean = 0 (dy == dx), add only with mean = 0 (dy = f32), and the latter
+// with the fused embedding update (adam = 1).  The grid is the
 // number of blocks resident at once on num_sms SMs, at most max_grid.
 // Returns the grid size used (the row count of colsum_partials), or -1 for
 // an operand set outside these three (nothing is launched).
@@ -123,6 +135,17 @@ struct GemmArgs {
   int n_valid = 0;
   int splits = 1;
   int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
+  // Fused embedding update (adam = 1, with add, mean = 0, dy = f32): the row
+  // result g_i is the embedding gradient; Adam updates emb/emb_m/emb_v
+  // ([N x H] f32, row stride H) and writes the updated row to shadow (dtype
+  // dx, row stride lds).  Y may be null (the gradient is then not stored).
+  int adam = 0;
+  float* emb = nullptr;
+  float* emb_m = nullptr;
+  float* emb_v = nullptr;
+  void* shadow = nullptr;
+  int64_t lds = 0;
+  float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
 };
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
 // out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.
@@ -133,12 +156,6 @@ void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp,
 void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g,
                  float lr, float beta1, float beta2, float eps, float wd,
                  float bc1, float bc2, cudaStream_t st);
-// Adam over the N x H0 embedding master, then writes the activation copy
-// (dtype dsh) into shadow[i*lds + k].
-void adam_emb_launch(int64_t N, int H0, float* X0, float* m, float* v,
-                     const float* g, float lr, float beta1, float beta2,
-                     float eps, float wd, float bc1, float bc2, void* shadow,
-                     int64_t lds, int dsh, cudaStream_t st);
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd,
                       int ddst, cudaStream_t st);
 // BF16 shadows of the dense weights:

@@ -44,6 +44,7 @@ def test_config_default_and_param_counts(L):
     assert (cfg.problem, cfg.S, cfg.H0, cfg.H1, cfg.alpha) == (cpra.MIS, 8, 16, 16, 2)
     assert cfg.lr == pytest.approx(1e-3) and cfg.beta2 == pytest.approx(0.999)
     assert cfg.gamma0 == pytest.approx(-2.0) and cfg.gamma1 == pytest.approx(0.1)
+    assert (cfg.train_embedding, cfg.keep_emb_grad) == (1, 0)
     golden = os.path.join(os.path.dirname(__file__), "golden", "param_counts.txt")
     for line in open(golden):
         line = line.split("--")[0].strip()
@@ -98,6 +99,8 @@ def test_invalid_config_rejected_on_host(L):
     rp, col = I.random_regular_graph(20, 3, seed=1)
     st, _ = _init_status(rp, col, alpha=3)
     assert st == cpra.CPRA_EINVAL
+    st, msg = _init_status(rp, col, keep_emb_grad=2)
+    assert st == cpra.CPRA_EINVAL and "keep_emb_grad" in msg
     cfg = cpra.make_config(problem=cpra.MIS)   # MIS without lambda
     with pytest.raises(cpra.CpraError) as ei:
         cpra.cpra_init_graph(rp, col, cfg, workspace=None)

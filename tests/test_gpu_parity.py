@@ -198,7 +198,7 @@ STEP_CASES = [
 ]
 
 
-def _run_step_case(case, precision):
+def _run_step_case(case, precision, keep_emb_grad=1):
     problem, div, alpha, nu, S, H, N, gk = case
     rp, col = graph_of(gk, N, seed=N + S)
     g = O.Graph(rp, col)
@@ -210,14 +210,16 @@ def _run_step_case(case, precision):
     gamma = O.gamma_schedule(t_idx, T, -1.0, 1.0)
     solver = cpra.Solver(rp, col, lam=lam if problem == O.MIS else None, problem=problem, S=S,
                          H0=H, H1=H, alpha=alpha, precision=precision, nu=nu,
-                         diversity_kind=div, gamma0=-1.0, gamma1=1.0, schedule_steps=T)
+                         diversity_kind=div, gamma0=-1.0, gamma1=1.0, schedule_steps=T,
+                         keep_emb_grad=keep_emb_grad)
     for which, arr in ((cpra.T_THETA, theta), (cpra.T_EMB, X0), (cpra.T_THETA_M, mt),
                        (cpra.T_THETA_V, vt), (cpra.T_EMB_M, mx), (cpra.T_EMB_V, vx),
                        (cpra.T_STEP, np.array([t_prev]))):
         solver.set(which, arr)
     terms = solver.step(t_idx, want_terms=True).astype(np.float64)
     out = dict(P=solver.P(), grad=solver.get(cpra.T_GRAD), gX0=solver.get(cpra.T_EMB_GRAD),
-               theta=solver.get(cpra.T_THETA), X0=solver.get(cpra.T_EMB), terms=terms)
+               theta=solver.get(cpra.T_THETA), X0=solver.get(cpra.T_EMB), terms=terms,
+               X0_m=solver.get(cpra.T_EMB_M), X0_v=solver.get(cpra.T_EMB_V))
     rec, ham, bits = solver.round_eval(want_bits=True)
     out.update(rec=rec, ham=ham, bits=bits)
     assert solver.get(cpra.T_STEP)[0] == t_prev + 1
@@ -278,6 +280,23 @@ def test_full_step_fp32_matches_oracle(case):
 def test_full_step_bf16_matches_oracle(case):
     out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, cpra.BF16)
     _check_step(out, ref, g, lam, gamma, theta, X0, case[4], case[5], 2e-2, case[0])
+
+
+@pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
+def test_fused_embedding_update_without_stored_gradient(precision):
+    """By default the step fuses the embedding Adam update into the last
+    backward aggregation and does not store dR/dh^0; the updated embeddings
+    and moments are bit-identical to the run that also stores the gradient,
+    and both match the oracle's Adam step (Experiments section optimiser)."""
+    case = STEP_CASES[0]
+    S, H = case[4], case[5]
+    kept, ref, g, lam, gamma, theta, X0 = _run_step_case(case, precision, keep_emb_grad=1)
+    fused, _, _, _, _, _, _ = _run_step_case(case, precision, keep_emb_grad=0)
+    for k in ("X0", "X0_m", "X0_v", "theta", "grad", "P"):
+        assert np.array_equal(kept[k], fused[k]), k
+    tol = 1e-5 if precision == cpra.FP32 else 2e-2
+    dref = ref["X0_next"] - X0
+    assert np.linalg.norm(fused["X0"].reshape(X0.shape) - ref["X0_next"]) <= 10 * tol * np.linalg.norm(dref)
 
 
 @pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
