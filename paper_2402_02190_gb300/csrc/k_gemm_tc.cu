@@ -156,6 +156,32 @@ struct TcParams {
 // columns; a TMA tensor store writes a buffer out while the warp fills the
 // other one.
 constexpr int kStgBytes = 32 * 16 * 4;
+
+// Staging of one 32-row x 16-column output box (lane = row) in the layout
+// the tensor store reads with its swizzle mode, which spreads the 16-byte
+// chunks of consecutive rows over all shared-memory banks: FP32 rows are 64
+// bytes (64-byte swizzle: chunk c of row r at c ^ ((r >> 1) & 3)), BF16 rows
+// 32 bytes (32-byte swizzle: chunk c at c ^ ((r >> 2) & 1)).  buf is at least
+// 512-byte aligned.
+__device__ __forceinline__ void stage_row_f32(uint8_t* buf, int r, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<float4*>(buf + r * 64 + 16 * (c ^ ((r >> 1) & 3))) =
+        make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+__device__ __forceinline__ void stage_row_bf16(uint8_t* buf, int r, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * c + 2 * q], v[8 * c + 2 * q + 1]);
+      w[q] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(buf + r * 32 + 16 * (c ^ ((r >> 2) & 1))) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
 constexpr int kStgTotal = kEpiWarps * 2 * kStgBytes;
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
@@ -194,7 +220,7 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int k = 4 * j + e;
-          v[k] = (n + k < p.n_valid) ? __frcp_rn(1.0f + __expf(-(v[k] + bb[e]))) : 0.f;
+          v[k] = (n + k < p.n_valid) ? __fdividef(1.0f, 1.0f + __expf(-(v[k] + bb[e]))) : 0.f;
         }
       }
       return 0;
@@ -397,8 +423,8 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           // the tensor store that last read this buffer must be done with it
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           __syncwarp();
-          if ((which ? p.d1 : p.d0) == DT_BF16) storeN<16>(reinterpret_cast<bf16*>(buf) + lane * 16, v);
-          else storeN<16>(reinterpret_cast<float*>(buf) + lane * 16, v);
+          if ((which ? p.d1 : p.d0) == DT_BF16) stage_row_bf16(buf, lane, v);
+          else stage_row_f32(buf, lane, v);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {  // rows past M are clipped by the tensor map
@@ -689,7 +715,8 @@ bool make_out_map(CUtensorMap* m, const void* base, int dt, int64_t cols, int64_
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(m, dt == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                         2, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        esz == 4 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
