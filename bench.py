@@ -40,25 +40,29 @@ from paper_2402_02190_gb300 import inputs as I  # noqa: E402
 METRIC = "edge·shot·steps/s"
 
 WORKLOADS = {
-    # name: (graph, N, degree, seed, problem, S, H, lambda, nu, precision)
+    # name: (graph, N, degree, seed, problem, S, H, lambda, nu, precision, diversity
+    # form, recompute); the N = 10^6 and the max-cut shapes recompute the
+    # layer-1 ReLU mask in the backward instead of keeping the activations.
     "mis_rrg5_n1e6_s256_h128_bf16": dict(graph="rrg", N=10**6, d=5, seed=5, problem=0, S=256,
                                          H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
-                                         div=0),
+                                         div=0, recompute=1),
     "mis_rrg5_n1e6_s256_h128_fp32": dict(graph="rrg", N=10**6, d=5, seed=5, problem=0, S=256,
                                          H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=0,
-                                         div=0),
+                                         div=0, recompute=1),
     # same shape at N/5 (P = 205 MB, still larger than L2): the small case
     # for full ncu captures
     "mis_rrg5_n2e5_s256_h128_bf16": dict(graph="rrg", N=2 * 10**5, d=5, seed=5, problem=0, S=256,
                                          H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
-                                         div=0),
+                                         div=0, recompute=1),
     "mis_rrg20_n1e4_s100_h256_bf16": dict(graph="rrg", N=10**4, d=20, seed=2, problem=0, S=100,
                                           H=256, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
-                                          div=0),
+                                          div=0, recompute=0),
     "maxcut_er10_n1e5_s64_h128_bf16": dict(graph="er", N=10**5, d=10, seed=3, problem=1, S=64,
-                                           H=128, lam=None, nu=0.1, precision=1, div=1),
+                                           H=128, lam=None, nu=0.1, precision=1, div=1,
+                                           recompute=1),
     "mis_rrg3_n100_s8_h16_fp32": dict(graph="rrg", N=100, d=3, seed=1, problem=0, S=8, H=16,
-                                      lam=("lin", 1.0, 8.0), nu=0.0, precision=0, div=0),
+                                      lam=("lin", 1.0, 8.0), nu=0.0, precision=0, div=0,
+                                      recompute=0),
 }
 DEFAULT_WORKLOAD = "mis_rrg5_n1e6_s256_h128_bf16"
 # Bounded CPU sample for the oracle: the same degree, width and shots on a
@@ -235,12 +239,13 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     w = WORKLOADS[args.workload]
+    recompute = w["recompute"] if args.recompute is None else args.recompute
     rp, col = make_graph(w)
     N, nnz, S, H = w["N"], int(rp[-1]), w["S"], w["H"]
     lam = make_lambda(w)
     kw = dict(problem=w["problem"], S=S, H0=H, H1=H, precision=w["precision"], nu=w["nu"],
               diversity_kind=w["div"], gamma0=-2.0, gamma1=0.1,
-              schedule_steps=args.warmup + args.steps, seed=1 + rank)
+              schedule_steps=args.warmup + args.steps, seed=1 + rank, recompute=recompute)
 
     solver = cpra.Solver(rp, col, lam=lam, **kw)
     stream = solver.stream          # the stream every library kernel is launched on
@@ -307,6 +312,7 @@ def run_gpu(args):
                    "nnz": nnz, "S": S, "H0": H, "H1": H,
                    "problem": ["MIS", "MaxCut"][w["problem"]], "nu": w["nu"],
                    "precision": ["fp32", "bf16"][w["precision"]], "parallelism": f"replicas{world}",
+                   "recompute": recompute,
                    "l2": f"inputs larger than L2 (P = {N * S * 4 / 1e9:.2f} GB), no flush"},
         "roofline": {"kernel": "loss_fused", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -368,6 +374,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--recompute", type=int, choices=[0, 1], default=None,
+                    help="override the workload's activation-recompute setting")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
     if args.impl == "reference":

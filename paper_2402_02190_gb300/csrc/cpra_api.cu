@@ -43,13 +43,15 @@ enum KernelId {
   K_ADAM,
   K_ADAM_EMB,
   K_EVAL,
+  K_RECOMPUTE_MASK,
   K_COUNT_
 };
 
 const char* kKernelNames[K_COUNT_] = {
     "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
     "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
-    "gemm_dgrad1", "spmm_bwd1",   "adam",       "spmm_bwd1_adam_embedding", "round_eval"};
+    "gemm_dgrad1", "spmm_bwd1",   "adam",       "spmm_bwd1_adam_embedding", "round_eval",
+    "recompute_layer1_mask"};
 
 constexpr size_t kAlign = 256;
 
@@ -113,8 +115,10 @@ struct cpra_ctx {
   void* HM = nullptr;
   float* P = nullptr;
   void* GZ2 = nullptr;
-  void* GHM = nullptr;
-  void* GXM = nullptr;
+  void* GHM = nullptr;   // aliases HM when recompute
+  void* GXM = nullptr;   // aliases XM when recompute
+  uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
+  bool recompute = false;
   uint32_t* xbits = nullptr;
   float* loss_part = nullptr;
   int64_t pstride = 0;
@@ -182,6 +186,7 @@ std::string validate_config(const cpra_config* cfg) {
   if (cfg->precision != CPRA_FP32 && cfg->precision != CPRA_BF16) return "precision must be FP32 or BF16";
   if (cfg->diversity_kind != CPRA_DIV_STD && cfg->diversity_kind != CPRA_DIV_VAR) return "bad diversity_kind";
   if (cfg->keep_emb_grad != 0 && cfg->keep_emb_grad != 1) return "keep_emb_grad must be 0 or 1";
+  if (cfg->recompute != 0 && cfg->recompute != 1) return "recompute must be 0 or 1";
   if (cfg->problem == CPRA_MIS && cfg->lambda == nullptr) return "MIS needs lambda[S]";
   if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
   if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
@@ -238,8 +243,19 @@ size_t carve(cpra_ctx* c, void* base) {
   c->HM = cv.take<char>((size_t)N * 2 * c->H1 * act);
   c->P = cv.take<float>((size_t)N * c->S_pad);
   c->GZ2 = cv.take<char>((size_t)N * c->S_pad * act);
-  c->GHM = cv.take<char>((size_t)N * 2 * c->H1 * act);
-  c->GXM = cv.take<char>((size_t)N * 2 * c->H0 * act);
+  if (c->recompute) {
+    // The layer activations [H1|M2] and [X0|M1] are dead by the time the
+    // backward writes the same-shaped gradient blocks (layer-2 weight
+    // gradient first, layer-1 weight gradient before dG_X0), so each pair
+    // shares one block; the ReLU mask the layer-1 adjoint needs is
+    // recomputed from Z1 as bits.
+    c->GHM = c->HM;
+    c->GXM = c->XM;
+    c->relu_bits = cv.take<uint16_t>((size_t)N * (c->H1 / 16));
+  } else {
+    c->GHM = cv.take<char>((size_t)N * 2 * c->H1 * act);
+    c->GXM = cv.take<char>((size_t)N * 2 * c->H0 * act);
+  }
   c->xbits = cv.take<uint32_t>((size_t)N * c->W);
   c->pstride = loss_pstride(c->S);
   c->loss_part = cv.take<float>((size_t)kLossMaxGrid * c->pstride);
@@ -270,6 +286,7 @@ void set_dims(cpra_ctx* c, int64_t N, int64_t nnz, const cpra_config* cfg) {
   c->H1 = cfg->H1;
   c->act_dt = cfg->precision == CPRA_BF16 ? DT_BF16 : DT_F32;
   c->nparam = layout_of(cfg->H0, cfg->H1, cfg->S).total;
+  c->recompute = cfg->recompute != 0;
 }
 
 // ---------------------------------------------------------------- profiling
@@ -470,6 +487,12 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
   const int max_grid = c->num_sms * 8;
   const Layout L = layout_of(H0, H1, c->S);
   const bool bf = c->act_dt == DT_BF16;
+  // The layer-2 weight gradient goes first: with recompute the gradient block
+  // [G_H1a | G_M2/deg] below overwrites [H1|M2].
+  {
+    Region r(c, K_WGRAD2);  // dWcat2 = G_Z2^T [H1|M2]
+    wgrad(c, c->GZ2, c->S_pad, c->S, c->HM, 2 * H1, 2 * H1, c->grad + L.wcat2, 2 * H1);
+  }
   {  // [G_H1a | G_M2/deg] = G_Z2 Wcat2
     Region r(c, K_GEMM_DGRAD2);
     GemmArgs g;
@@ -483,13 +506,26 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     g.row_scale = c->inv_deg; g.n_valid = 2 * H1;
     dense(c, g);
   }
+  if (c->recompute) {  // 1[Z1 > 0] from Z1 = [X0|M1] Wcat1^T + b1, recomputed (a7)
+    Region r(c, K_RECOMPUTE_MASK);
+    GemmArgs g;
+    g.M = N; g.Nc = H1; g.K = 2 * H0;
+    g.A = c->XM; g.lda = 2 * H0; g.da = c->act_dt; g.a_kmajor = 1;
+    if (bf) { g.B = c->W1s; g.db = DT_BF16; }
+    else { g.B = c->theta + L.wcat1; g.db = DT_F32; }
+    g.ldb = 2 * H0; g.b_kmajor = 1;
+    g.epi = EPI_RELU_BITS; g.bias = c->theta + L.b1;
+    g.out0 = c->relu_bits; g.ld0 = H1 / 16; g.d0 = c->act_dt; g.n_valid = H1;
+    dense(c, g);
+  }
   {  // G_Z1 = (G_H1a + sum_j G_M2_j/deg_j) * 1[H1 > 0], db1 = colsum(G_Z1)
     Region r(c, K_SPMM_BWD2);
     SpmmArgs a;
     a.N = N; a.H = H1; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
     a.X = act_off(c->GHM, H1, c); a.ldx = 2 * H1;
     a.add = c->GHM; a.ldadd = 2 * H1;
-    a.mask = c->HM; a.ldm = 2 * H1;
+    if (c->recompute) { a.mask_bits = c->relu_bits; a.ldmb = H1 / 16; }
+    else { a.mask = c->HM; a.ldm = 2 * H1; }
     a.Y = c->GHM; a.ldy = 2 * H1; a.mean = 0;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     a.colsum_partials = c->colsum_part;
@@ -498,10 +534,6 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
                     c->stream);
     c->launches += 2;
-  }
-  {
-    Region r(c, K_WGRAD2);  // dWcat2 = G_Z2^T [H1|M2]
-    wgrad(c, c->GZ2, c->S_pad, c->S, c->HM, 2 * H1, 2 * H1, c->grad + L.wcat2, 2 * H1);
   }
   {
     Region r(c, K_WGRAD1);  // dWcat1 = G_Z1^T [X0|M1]
@@ -541,6 +573,9 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
       c->launches += 1;
     }
+    // With recompute the gradient block overwrote the embedding copy that
+    // the forward reads; the fused update rewrites it, otherwise restore it.
+    if (c->recompute && !fuse_adam) refresh_emb_shadow(c);
   }
   return CPRA_OK;
 }

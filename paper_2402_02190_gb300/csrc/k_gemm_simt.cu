@@ -88,6 +88,31 @@ gemm_simt_kernel(GemmArgs g) {
     __syncthreads();
   }
 
+  if (g.epi == EPI_RELU_BITS) {
+    // lanes 0-15 of a warp hold row ty, lanes 16-31 row ty + 1, each 16
+    // consecutive columns n0 + 16c + tx: one ballot gives both rows' masks
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t m = m0 + ty + 16 * r;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int n = n0 + tx + 16 * c;
+        bool bit = false;
+        if (m < g.M && n < g.Nc) {
+          float v = acc[r][c] + g.bias[n];
+          v = v > 0.f ? v : 0.f;
+          if (g.d0 == DT_BF16) v = __bfloat162float(__float2bfloat16_rn(v));
+          bit = v > 0.f;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, bit);
+        if (tx == 0 && m < g.M && n < g.Nc)
+          static_cast<uint16_t*>(g.out0)[m * g.ld0 + n / 16] =
+              static_cast<uint16_t>(lane >= 16 ? b >> 16 : b & 0xffffu);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int64_t m = m0 + ty + 16 * r;

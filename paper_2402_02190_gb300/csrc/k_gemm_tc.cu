@@ -199,7 +199,8 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
                                           int* out_col) {
   *out_col = n;
   switch (EPI) {
-    case EPI_BIAS_RELU: {
+    case EPI_BIAS_RELU:
+    case EPI_RELU_BITS: {
       const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -419,6 +420,20 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
           int col;
           const int which = epilogue16<EPI>(p, row, n0 + c, v, &col);
+          if constexpr (EPI == EPI_RELU_BITS) {
+            // mask of the activation as stored in dtype d0; no tile store
+            uint32_t bits = 0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              float h = v[i];
+              if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
+              bits |= (h > 0.f ? 1u : 0u) << i;
+            }
+            if (row < p.M)
+              static_cast<uint16_t*>(p.out0)[row * p.ld0 + (n0 + c) / 16] =
+                  static_cast<uint16_t>(bits);
+            continue;
+          }
           uint8_t* buf = stg + sb * kStgBytes;
           // the tensor store that last read this buffer must be done with it
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
@@ -681,6 +696,8 @@ void init_driver() {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
       cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_SPLIT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_RELU_BITS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
       cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            g_max_smem) != cudaSuccess) {
     cudaGetLastError();
@@ -741,11 +758,13 @@ bool tc_prepare(int, std::string* msg) {
 bool tc_gemm_supported(const GemmArgs& g) {
   if (!g_ok) return false;
   if (g.da != DT_BF16 || g.db != DT_BF16 || !g.a_kmajor || !g.b_kmajor) return false;
-  if (g.epi != EPI_BIAS_RELU && g.epi != EPI_BIAS_SIGMOID && g.epi != EPI_SPLIT) return false;
+  if (g.epi != EPI_BIAS_RELU && g.epi != EPI_BIAS_SIGMOID && g.epi != EPI_SPLIT &&
+      g.epi != EPI_RELU_BITS)
+    return false;
   if (g.K < kBK || g.K % 8 || g.lda % 8 || g.ldb % 8) return false;
   if (g.Nc % 16 || pick_bn(g.Nc) == 0) return false;
   if (g.epi == EPI_SPLIT && g.split % 16) return false;
-  if (g.ld0 % 8 || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
+  if ((g.epi != EPI_RELU_BITS && g.ld0 % 8) || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
   const int bn = pick_bn(g.Nc);
   const int n_kb = static_cast<int>((g.K + kBK - 1) / kBK);
   const size_t need =
@@ -790,8 +809,11 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.err_flag = g.err_flag;
   CUtensorMap ta, tb, to0, to1;
   const int64_t cols0 = g.epi == EPI_SPLIT ? g.split : g.Nc;
-  bool ok = make_map(&ta, g.A, g.K, g.M, g.lda, kBM) && make_map(&tb, g.B, g.K, g.Nc, g.ldb, p.BN) &&
-            make_out_map(&to0, g.out0, g.d0, cols0, g.M, g.ld0);
+  bool ok = make_map(&ta, g.A, g.K, g.M, g.lda, kBM) && make_map(&tb, g.B, g.K, g.Nc, g.ldb, p.BN);
+  if (ok) {
+    if (g.epi == EPI_RELU_BITS) to0 = tb;  // bits are stored directly; map unused
+    else ok = make_out_map(&to0, g.out0, g.d0, cols0, g.M, g.ld0);
+  }
   if (ok) {
     if (g.epi == EPI_SPLIT) ok = make_out_map(&to1, g.out1, g.d1, g.Nc - g.split, g.M, g.ld1);
     else to1 = to0;
@@ -811,6 +833,9 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
       break;
     case EPI_BIAS_SIGMOID:
       tc_gemm_nt_kernel<EPI_BIAS_SIGMOID><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+    case EPI_RELU_BITS:
+      tc_gemm_nt_kernel<EPI_RELU_BITS><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
       break;
     default:
       tc_gemm_nt_kernel<EPI_SPLIT><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);

@@ -23,6 +23,7 @@ enum SpmmKind {
   KIND_ADD_MASK_COLSUM = 1,  // Y = (add + A X) * 1[mask > 0], column sums of Y
   KIND_ADD = 2,              // Y = add + A X
   KIND_ADD_ADAM = 3,         // g = add + A X; Adam step on the embedding row with g
+  KIND_ADD_MASKBITS_COLSUM = 4,  // as KIND_ADD_MASK_COLSUM with the mask given as bits
 };
 
 template <typename TX, typename TY, int LPR, int CPL, int KIND>
@@ -31,7 +32,8 @@ spmm_rows_kernel(SpmmArgs a) {
   constexpr bool MEAN = KIND == KIND_MEAN;
   constexpr bool HAS_ADD = KIND != KIND_MEAN;
   constexpr bool HAS_MASK = KIND == KIND_ADD_MASK_COLSUM;
-  constexpr bool COLSUM = KIND == KIND_ADD_MASK_COLSUM;
+  constexpr bool MASK_BITS = KIND == KIND_ADD_MASKBITS_COLSUM;
+  constexpr bool COLSUM = KIND == KIND_ADD_MASK_COLSUM || KIND == KIND_ADD_MASKBITS_COLSUM;
   constexpr bool ADAM = KIND == KIND_ADD_ADAM;
   constexpr int VEC = V16<TX>::n;
   const int lane = threadIdx.x & 31;
@@ -58,13 +60,17 @@ spmm_rows_kernel(SpmmArgs a) {
   for (int64_t i = first; i < a.N; i += stride) {
     // the row's own operands first, so that they arrive with the gathers
     uint4 rad[CPL], rmk[CPL];
+    uint32_t mbits[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       const int ch = c * LPR + sub;
       rad[c] = rmk[c] = make_uint4(0, 0, 0, 0);
+      mbits[c] = 0u;
       if (ch < nchunks) {
         if constexpr (HAS_ADD) rad[c] = ld_stream16(ADD + i * a.ldadd + ch * VEC, pol);
         if constexpr (HAS_MASK) rmk[c] = ld_stream16(MASK + i * a.ldm + ch * VEC, pol);
+        if constexpr (MASK_BITS)
+          mbits[c] = (uint32_t)a.mask_bits[i * a.ldmb + (ch * VEC) / 16] >> ((ch * VEC) % 16);
       }
     }
     float acc[CPL][VEC];
@@ -142,6 +148,10 @@ spmm_rows_kernel(SpmmArgs a) {
         widen(rmk[c], mk, (const TX*)nullptr);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = (mk[v] > 0.f) ? o[v] : 0.f;
+      }
+      if constexpr (MASK_BITS) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = ((mbits[c] >> v) & 1u) ? o[v] : 0.f;
       }
       if constexpr (COLSUM) {
 #pragma unroll
@@ -225,7 +235,9 @@ template <typename TX, typename TY, int LPR, int CPL, int KIND>
 int launch_t(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   constexpr int threads = 256;
   const int segs_per_block = (threads / 32) * (32 / LPR);
-  const size_t smem = (KIND == KIND_ADD_MASK_COLSUM) ? (size_t)(threads / 32) * a.H * sizeof(float) : 0;
+  const size_t smem = (KIND == KIND_ADD_MASK_COLSUM || KIND == KIND_ADD_MASKBITS_COLSUM)
+                           ? (size_t)(threads / 32) * a.H * sizeof(float)
+                           : 0;
   auto kernel = spmm_rows_kernel<TX, TY, LPR, CPL, KIND>;
   static std::atomic<long long> occ_cache{-1};
   const int64_t resident = (int64_t)resident_blocks(kernel, threads, smem, occ_cache) * num_sms;
@@ -260,6 +272,12 @@ int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
     return a.dx == DT_BF16 ? dispatch_lpr<bf16, bf16, KIND_MEAN>(a, num_sms, max_grid, st)
                            : dispatch_lpr<float, float, KIND_MEAN>(a, num_sms, max_grid, st);
   }
+  if (!a.mean && add && !mask && a.mask_bits && cs && same) {
+    return a.dx == DT_BF16
+               ? dispatch_lpr<bf16, bf16, KIND_ADD_MASKBITS_COLSUM>(a, num_sms, max_grid, st)
+               : dispatch_lpr<float, float, KIND_ADD_MASKBITS_COLSUM>(a, num_sms, max_grid, st);
+  }
+  if (a.mask_bits) return -1;
   if (!a.mean && add && mask && cs && same) {
     return a.dx == DT_BF16
                ? dispatch_lpr<bf16, bf16, KIND_ADD_MASK_COLSUM>(a, num_sms, max_grid, st)

@@ -35,6 +35,10 @@ struct SpmmArgs {
   int dx = DT_F32;
   int dy = DT_F32;
   int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
+  // Mask given as bits instead of values (with add and colsum, mean = 0): bit
+  // (k % 16) of mask_bits[i*ldmb + k/16] is 1[mask_ik > 0] (EPI_RELU_BITS).
+  const uint16_t* mask_bits = nullptr;
+  int64_t ldmb = 0;
   // Fused embedding update (adam = 1, with add, mean = 0, dy = f32): the row
   // result g_i is the embedding gradient; Adam updates emb/emb_m/emb_v
   // ([N x H] f32, row stride H) and writes the updated row to shadow (dtype
@@ -47,10 +51,10 @@ struct SpmmArgs {
   int64_t lds = 0;
   float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
 };
-// Four operand sets are supported (the ones the training step uses):
+// Five operand sets are supported (the ones the training step uses):
 // mean aggregation (no add/mask/colsum, dy == dx), add + mask + colsum with
-// mean = 0 (dy == dx), add only with mean = 0 (dy = f32), and the latter
-// with the fused embedding update (adam = 1).  The grid is the
+// mean = 0 (dy == dx; the mask as values or as bits), add only with mean = 0
+// (dy = f32), and the latter with the fused embedding update (adam = 1).  The grid is the
 // number of blocks resident at once on num_sms SMs, at most max_grid.
 // Returns the grid size used (the row count of colsum_partials), or -1 for
 // an operand set outside these three (nothing is launched).
@@ -102,7 +106,8 @@ void eval_finalize(const unsigned long long* counters, int S, int problem,
                    cudaStream_t st);
 
 // ---------------------------------------------------------------- GEMM
-enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3 };
+enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3,
+           EPI_RELU_BITS = 4 };
 // C[m, n] = sum_k A(m, k) B(n, k), FP32 accumulation.
 //   A(m, k) = A[m*lda + k] if a_kmajor else A[k*lda + m]; same for B.
 // Epilogues:
@@ -110,6 +115,9 @@ enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT =
 //   EPI_BIAS_RELU    out0[m, n] <- max(C + bias[n], 0)
 //   EPI_BIAS_SIGMOID out0[m, n] <- 1/(1+exp(-(C + bias[n]))) for n < n_valid, else 0
 //   EPI_SPLIT        n < split: out0[m, n] <- C; else out1[m, n-split] <- C * row_scale[m]
+//   EPI_RELU_BITS    ReLU mask only: bit (n % 16) of the uint16 out0[m*ld0 + n/16] is
+//                    1[h > 0] for h = max(C + bias[n], 0) rounded to dtype d0 (so the
+//                    mask equals the one read from a stored activation); Nc % 16 == 0
 struct GemmArgs {
   int64_t M = 0;
   int Nc = 0;
@@ -135,17 +143,6 @@ struct GemmArgs {
   int n_valid = 0;
   int splits = 1;
   int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
-  // Fused embedding update (adam = 1, with add, mean = 0, dy = f32): the row
-  // result g_i is the embedding gradient; Adam updates emb/emb_m/emb_v
-  // ([N x H] f32, row stride H) and writes the updated row to shadow (dtype
-  // dx, row stride lds).  Y may be null (the gradient is then not stored).
-  int adam = 0;
-  float* emb = nullptr;
-  float* emb_m = nullptr;
-  float* emb_v = nullptr;
-  void* shadow = nullptr;
-  int64_t lds = 0;
-  float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
 };
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
 // out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.

@@ -64,6 +64,22 @@ def test_workspace_bytes_valid_and_invalid(L):
     assert cpra.cpra_workspace_bytes(100, 300, bad) == 0
 
 
+def test_recompute_shares_activation_and_gradient_blocks(L):
+    """recompute = 1 keeps no layer activations for the backward: [X0|M1]
+    and [H1|M2] share memory with the same-shaped gradient blocks, and only
+    the N x H1 ReLU mask bits are added."""
+    N, nnz, H0, H1 = 10**6, 5 * 10**6, 128, 128
+    for prec, act in ((cpra.BF16, 2), (cpra.FP32, 4)):
+        kw = dict(S=256, H0=H0, H1=H1, precision=prec, problem=cpra.MAXCUT)
+        full = cpra.cpra_workspace_bytes(N, nnz, cpra.make_config(recompute=0, **kw))
+        lean = cpra.cpra_workspace_bytes(N, nnz, cpra.make_config(recompute=1, **kw))
+        saved = 2 * N * (H0 + H1) * act - N * (H1 // 16) * 2
+        assert abs((full - lean) - saved) <= 4 * 256
+    rp, col = I.random_regular_graph(20, 3, seed=1)
+    st, msg = _init_status(rp, col, recompute=2)
+    assert st == cpra.CPRA_EINVAL and "recompute" in msg
+
+
 def _init_status(rowptr, col, **kw):
     cfg = cpra.make_config(problem=cpra.MAXCUT, **kw)
     try:

@@ -58,6 +58,35 @@ def test_autograd_gradient_matches_oracle(precision, tol, problem, div):
     solver.close()
 
 
+@pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
+def test_autograd_recompute_matches_stored(precision):
+    """With recompute = 1 the adjoint (whose gradient block overwrites the
+    embedding copy the forward reads) gives the same gradients, and the next
+    forward sees the restored copy: two forward/backward rounds are
+    bit-identical to the stored-activation form."""
+    res = []
+    for rc in (0, 1):
+        rp, col = I.random_regular_graph(600, 4, 3)
+        lam = I.lambda_geomspace(0.5, 10.0, 40)
+        solver = cpra.Solver(rp, col, lam=lam, problem=cpra.MIS, S=40, H0=32, H1=32,
+                             precision=precision, nu=0.3, recompute=rc)
+        theta, X0 = I.seeded_params(600, 32, 32, 40, seed=13, weight_scale=1.5)
+        out = []
+        for _ in range(2):
+            th = torch.tensor(theta, device="cuda", requires_grad=True)
+            em = torch.tensor(X0, device="cuda", requires_grad=True)
+            R, _ = cpra_loss(solver, th, em, -0.3)
+            R.backward()
+            out += [R.item(), th.grad.cpu().numpy(), em.grad.cpu().numpy()]
+        # a training step after the autograd backward reads the restored copy
+        solver.step(0)
+        out.append(solver.P())
+        res.append(out)
+        solver.close()
+    for a, b in zip(*res):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
 def test_autograd_directional_finite_differences():
     """(R(p + h v) - R(p - h v)) / 2h against grad . v, for random directions
     v over (theta, h^0), all through the library's FP32 forward."""

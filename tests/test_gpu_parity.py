@@ -198,7 +198,7 @@ STEP_CASES = [
 ]
 
 
-def _run_step_case(case, precision, keep_emb_grad=1):
+def _run_step_case(case, precision, keep_emb_grad=1, recompute=0):
     problem, div, alpha, nu, S, H, N, gk = case
     rp, col = graph_of(gk, N, seed=N + S)
     g = O.Graph(rp, col)
@@ -211,7 +211,7 @@ def _run_step_case(case, precision, keep_emb_grad=1):
     solver = cpra.Solver(rp, col, lam=lam if problem == O.MIS else None, problem=problem, S=S,
                          H0=H, H1=H, alpha=alpha, precision=precision, nu=nu,
                          diversity_kind=div, gamma0=-1.0, gamma1=1.0, schedule_steps=T,
-                         keep_emb_grad=keep_emb_grad)
+                         keep_emb_grad=keep_emb_grad, recompute=recompute)
     for which, arr in ((cpra.T_THETA, theta), (cpra.T_EMB, X0), (cpra.T_THETA_M, mt),
                        (cpra.T_THETA_V, vt), (cpra.T_EMB_M, mx), (cpra.T_EMB_V, vx),
                        (cpra.T_STEP, np.array([t_prev]))):
@@ -297,6 +297,40 @@ def test_fused_embedding_update_without_stored_gradient(precision):
     tol = 1e-5 if precision == cpra.FP32 else 2e-2
     dref = ref["X0_next"] - X0
     assert np.linalg.norm(fused["X0"].reshape(X0.shape) - ref["X0_next"]) <= 10 * tol * np.linalg.norm(dref)
+
+
+@pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
+def test_recompute_step_matches_oracle_and_stored_form(precision):
+    """recompute = 1 (the layer-1 adjoint's ReLU mask recomputed from Z1, the
+    activation blocks shared with the gradient blocks) gives the same step
+    bit for bit as the stored-activation form, and matches the oracle."""
+    case = STEP_CASES[1]
+    S, H = case[4], case[5]
+    tol = 1e-5 if precision == cpra.FP32 else 2e-2
+    stored, ref, g, lam, gamma, theta, X0 = _run_step_case(case, precision, recompute=0)
+    lean, _, _, _, _, _, _ = _run_step_case(case, precision, recompute=1)
+    for k in ("P", "grad", "gX0", "theta", "X0", "X0_m", "X0_v", "terms", "bits"):
+        assert np.array_equal(stored[k], lean[k]), k
+    _check_step(lean, ref, g, lam, gamma, theta, X0, S, H, tol, case[0])
+
+
+@pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
+def test_recompute_many_steps_bitwise(precision):
+    """Five steps with and without recompute from the same seed stay
+    bit-identical (P, parameters, embeddings and the rounded bits)."""
+    rp, col = I.random_regular_graph(3000, 5, seed=21)
+    lam = I.lambda_linspace(1, 8, 48)
+    outs = []
+    for rc in (0, 1):
+        s = cpra.Solver(rp, col, lam=lam, problem=cpra.MIS, S=48, H0=32, H1=48,
+                        precision=precision, nu=0.2, seed=7, recompute=rc)
+        for t in range(5):
+            s.step(t)
+        rec, ham, bits = s.round_eval(want_bits=True)
+        outs.append((s.P(), s.get(cpra.T_THETA), s.get(cpra.T_EMB), bits, rec["objective"]))
+        s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
