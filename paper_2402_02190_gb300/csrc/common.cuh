@@ -113,7 +113,12 @@ __device__ __forceinline__ void st_stream16(void* p, const uint4& v, uint64_t po
                "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
                : "memory");
 }
-// storeN for N a multiple of 4 (float) or 8 (bf16), with the L2 hint.
+__device__ __forceinline__ void st_stream8(void* p, const uint2& v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1,%2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y),
+               "l"(pol)
+               : "memory");
+}
+// storeN for N a multiple of 4, with the L2 hint.
 template <int N>
 __device__ __forceinline__ void storeN_stream(float* p, const float* v, uint64_t pol) {
 #pragma unroll
@@ -124,16 +129,27 @@ __device__ __forceinline__ void storeN_stream(float* p, const float* v, uint64_t
 }
 template <int N>
 __device__ __forceinline__ void storeN_stream(bf16* p, const float* v, uint64_t pol) {
-  static_assert(N % 8 == 0, "bf16 streamed stores move 8 elements");
+  static_assert(N % 4 == 0, "bf16 streamed stores move 4 or 8 elements");
+  if constexpr (N % 8 == 0) {
 #pragma unroll
-  for (int k = 0; k < N; k += 8) {
-    uint32_t w[4];
+    for (int k = 0; k < N; k += 8) {
+      uint32_t w[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[k + 2 * q], v[k + 2 * q + 1]);
-      w[q] = *reinterpret_cast<uint32_t*>(&h);
+      for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[k + 2 * q], v[k + 2 * q + 1]);
+        w[q] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      st_stream16(p + k, make_uint4(w[0], w[1], w[2], w[3]), pol);
     }
-    st_stream16(p + k, make_uint4(w[0], w[1], w[2], w[3]), pol);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[k], v[k + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(v[k + 2], v[k + 3]);
+      st_stream8(p + k,
+                 make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1)),
+                 pol);
+    }
   }
 }
 

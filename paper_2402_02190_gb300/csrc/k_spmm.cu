@@ -27,7 +27,7 @@ enum SpmmKind {
 };
 
 template <typename TX, typename TY, int LPR, int CPL, int KIND>
-__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_MEAN || KIND == KIND_ADD ? 5 : 4))
+__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_MEAN ? 6 : KIND == KIND_ADD ? 5 : 4))
 spmm_rows_kernel(SpmmArgs a) {
   constexpr bool MEAN = KIND == KIND_MEAN;
   constexpr bool HAS_ADD = KIND != KIND_MEAN;
