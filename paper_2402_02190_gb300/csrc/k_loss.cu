@@ -358,11 +358,15 @@ __device__ __forceinline__ void ring_copy(void* dst, const void* src, uint32_t b
 // own P row and up to CAP neighbour rows, all copied with cp.async.bulk on a
 // single mbarrier (one wait per row).  While row r is processed, the rows
 // r + wstride .. r + (RS-1) wstride are in flight.  Neighbours beyond CAP
-// (high-degree rows) are gathered directly from global memory.
+// (high-degree rows) are gathered directly from global memory.  The CSR
+// index loads run ahead of the copies (row offsets two rows ahead, column
+// indices one row ahead), so issuing a row's copies never waits on them.
+constexpr int kRS = 2;
 template <int CPL, int PROBLEM, typename TG>
 __global__ void __launch_bounds__(256, 2)
-loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes) {
+loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
   constexpr int LPR = 32;
+  constexpr int RS = kRS;
   const int lane = threadIdx.x & 31;
   const int sub = lane;
   const unsigned smask = 0xffffffffu;
@@ -390,13 +394,11 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
   const int64_t first = (int64_t)blockIdx.x * nwarps + warp;
   const float* __restrict__ P = a.P;
 
-  // Lane 0 issues the copies of row r into row slot k; every lane takes
-  // part in reading the neighbour indices.
-  auto issue_row = [&](int64_t r, int k) {
+  // Lane 0 issues the copies of row r (CSR range beg..end, the first
+  // neighbour indices in jl across the lanes) into row slot k.
+  auto issue_row = [&](int64_t r, int beg, int end, int jl, int k) {
     if (r >= a.N) return;
-    const int beg = a.rowptr[r];
-    const int n = min(a.rowptr[r + 1] - beg, CAP);
-    const int jl = (lane < n) ? a.col[beg + lane] : 0;
+    const int n = min(end - beg, CAP);
     unsigned char* base = slots + (size_t)k * rslot_bytes;
     if (lane == 0) {
       ring_expect(bars + k, (uint32_t)(1 + n) * row_bytes);
@@ -406,6 +408,9 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
       const int j = __shfl_sync(smask, jl, t);
       if (lane == 0) ring_copy(base + (size_t)(1 + t) * row_bytes, P + (int64_t)j * a.ldp, row_bytes, bars + k);
     }
+  };
+  auto load_cols = [&](int beg, int end) -> int {
+    return (lane < min(end - beg, CAP)) ? a.col[beg + lane] : 0;
   };
   auto read_row = [&](const unsigned char* src, float (&f)[CPL][4]) {
 #pragma unroll
@@ -421,14 +426,30 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
     }
   };
 
-  for (int k = 0; k < RS; ++k) issue_row(first + k * wstride, k);
+  // CSR ranges of the rows in the two slots
+  int sbeg0 = 0, send0 = 0, sbeg1 = 0, send1 = 0;
+  {
+    const int64_t r0 = first, r1 = first + wstride;
+    if (r0 < a.N) { sbeg0 = a.rowptr[r0]; send0 = a.rowptr[r0 + 1]; }
+    if (r1 < a.N) { sbeg1 = a.rowptr[r1]; send1 = a.rowptr[r1 + 1]; }
+    const int j0 = load_cols(sbeg0, send0), j1 = load_cols(sbeg1, send1);
+    issue_row(r0, sbeg0, send0, j0, 0);
+    issue_row(r1, sbeg1, send1, j1, 1);
+  }
+  // index pipeline: row `nxt` (next to issue) has its range and column
+  // indices loaded; row nxt + wstride has its range loaded
+  int64_t nxt = first + RS * wstride;
+  int nbeg = 0, nend = 0, njl = 0, pbeg = 0, pend = 0;
+  if (nxt < a.N) { nbeg = a.rowptr[nxt]; nend = a.rowptr[nxt + 1]; }
+  njl = load_cols(nbeg, nend);
+  if (nxt + wstride < a.N) { pbeg = a.rowptr[nxt + wstride]; pend = a.rowptr[nxt + wstride + 1]; }
+
   int k = 0;
   uint32_t par = 0;
   bool dead = false;
-  int64_t next = first + RS * wstride;
   for (int64_t i = first; i < a.N; i += wstride) {
-    const int beg = a.rowptr[i];
-    const int end = a.rowptr[i + 1];
+    const int beg = k ? sbeg1 : sbeg0;
+    const int end = k ? send1 : send0;
     const int n = min(end - beg, CAP);
     if (!ring_wait(bars + k, par)) {
       dead = true;
@@ -451,8 +472,19 @@ loss_kernel_staged(LossArgs a, int RS, int CAP, int rslot_bytes, int bars_bytes)
         for (int e = 0; e < 4; ++e) q[c][e] += f[c][e];
     }
     __syncwarp();
-    issue_row(next, k);  // refill the slot just read
-    next += wstride;
+    issue_row(nxt, nbeg, nend, njl, k);  // refill the slot just read
+    if (k) { sbeg1 = nbeg; send1 = nend; } else { sbeg0 = nbeg; send0 = nend; }
+    // advance the index pipeline; these loads complete behind this row's
+    // epilogue
+    nxt += wstride;
+    nbeg = pbeg;
+    nend = pend;
+    njl = (nxt < a.N) ? load_cols(nbeg, nend) : 0;
+    pbeg = pend = 0;
+    if (nxt + wstride < a.N) {
+      pbeg = a.rowptr[nxt + wstride];
+      pend = a.rowptr[nxt + wstride + 1];
+    }
     if (++k == RS) {
       k = 0;
       par ^= 1u;
@@ -508,7 +540,7 @@ template <int CPL, int PROBLEM, typename TG>
 int launch_staged_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   constexpr int threads = 256;
   constexpr int nwarps = threads / 32;
-  constexpr int RS = 2;
+  constexpr int RS = kRS;
   const int row_bytes = (a.S + 3) / 4 * 16;
   const int bars_bytes = 128;  // nwarps * RS barriers
   int CAP = ((kStagedBudget - bars_bytes) / nwarps / RS) / row_bytes - 1;
@@ -533,7 +565,7 @@ int launch_staged_t(const LossArgs& a, int max_grid, cudaStream_t st) {
   int64_t want = (a.N + nwarps - 1) / nwarps;
   int grid = (int)(want < max_grid ? want : max_grid);
   if (grid < 1) grid = 1;
-  loss_kernel_staged<CPL, PROBLEM, TG><<<grid, threads, smem, st>>>(a, RS, CAP, rslot_bytes, bars_bytes);
+  loss_kernel_staged<CPL, PROBLEM, TG><<<grid, threads, smem, st>>>(a, CAP, rslot_bytes, bars_bytes);
   return grid;
 }
 
