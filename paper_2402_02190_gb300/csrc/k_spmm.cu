@@ -57,7 +57,26 @@ spmm_rows_kernel(SpmmArgs a) {
 #pragma unroll
     for (int v = 0; v < VEC; ++v) csum[c][v] = 0.f;
 
+  // CSR index pipeline: the current row's range and first LPR column
+  // indices, and the next row's range, are loaded one iteration ahead, so the
+  // gathers never wait on an index load.
+  int beg = 0, end = 0, jl = 0, pbeg = 0, pend = 0;
+  if (first < a.N) {
+    beg = a.rowptr[first];
+    end = a.rowptr[first + 1];
+    jl = (sub < end - beg) ? a.col[beg + sub] : 0;
+  }
+  if (first + stride < a.N) {
+    pbeg = a.rowptr[first + stride];
+    pend = a.rowptr[first + stride + 1];
+  }
   for (int64_t i = first; i < a.N; i += stride) {
+    const int njl = (i + stride < a.N && sub < pend - pbeg) ? a.col[pbeg + sub] : 0;
+    int ppbeg = 0, ppend = 0;
+    if (i + 2 * stride < a.N) {
+      ppbeg = a.rowptr[i + 2 * stride];
+      ppend = a.rowptr[i + 2 * stride + 1];
+    }
     // the row's own operands first, so that they arrive with the gathers
     uint4 rad[CPL], rmk[CPL];
     uint32_t mbits[CPL];
@@ -79,18 +98,16 @@ spmm_rows_kernel(SpmmArgs a) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
 
-    const int beg = a.rowptr[i];
-    const int end = a.rowptr[i + 1];
     for (int eb = beg; eb < end; eb += LPR) {
       const int e = eb + sub;
-      const int jl = (e < end) ? a.col[e] : 0;
+      const int jc = (eb == beg) ? jl : ((e < end) ? a.col[e] : 0);
       const int cnt = min(LPR, end - eb);
       int k = 0;
       for (; k + 4 <= cnt; k += 4) {
         uint4 raw[4][CPL];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int j = __shfl_sync(smask, jl, k + u, LPR);
+          const int j = __shfl_sync(smask, jc, k + u, LPR);
           const TX* row = X + (int64_t)j * a.ldx;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
@@ -109,7 +126,7 @@ spmm_rows_kernel(SpmmArgs a) {
           }
       }
       for (; k < cnt; ++k) {
-        const int j = __shfl_sync(smask, jl, k, LPR);
+        const int j = __shfl_sync(smask, jc, k, LPR);
         const TX* row = X + (int64_t)j * a.ldx;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -181,6 +198,11 @@ spmm_rows_kernel(SpmmArgs a) {
         storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
       }
     }
+    beg = pbeg;
+    end = pend;
+    jl = njl;
+    pbeg = ppbeg;
+    pend = ppend;
   }
 
   if constexpr (COLSUM) {
