@@ -79,25 +79,33 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
   Planes obj, viol;
   long long ham = 0;
   constexpr int U = 8;  // neighbour words loaded together
-  int beg = 0, end = 0;
+  // CSR index pipeline: the current row's range and first U column indices,
+  // and the next row's range, are loaded one iteration ahead
+  int beg = 0, end = 0, jfirst = -1, pbeg = 0, pend = 0;
   if (first < N) {
     beg = rowptr[first];
     end = rowptr[first + 1];
+    jfirst = ((sub % U) < end - beg) ? col[beg + (sub % U)] : -1;
+  }
+  if (first + stride < N) {
+    pbeg = rowptr[first + stride];
+    pend = rowptr[first + stride + 1];
   }
   for (int64_t i = first; i < N; i += stride) {
-    const int64_t next = i + stride;
-    int nbeg = 0, nend = 0;
-    if (next < N) {  // next row's bounds, fetched early
-      nbeg = rowptr[next];
-      nend = rowptr[next + 1];
+    const int njfirst =
+        (i + stride < N && (sub % U) < pend - pbeg) ? col[pbeg + (sub % U)] : -1;
+    int ppbeg = 0, ppend = 0;
+    if (i + 2 * stride < N) {
+      ppbeg = rowptr[i + 2 * stride];
+      ppend = rowptr[i + 2 * stride + 1];
     }
     const uint32_t xi = active ? bits[i * W + sub] : 0u;
     for (int eb = beg; eb < end; eb += U) {
-      // lanes of the segment load up to U neighbour indices, then every lane
+      // lanes of the segment hold up to U neighbour indices, then every lane
       // loads its word of each neighbour j > i (each edge once, at its lower
       // endpoint); all loads are in flight before any counter is updated
       const int e = eb + (sub % U);
-      const int jl = (e < end) ? col[e] : -1;
+      const int jl = (eb == beg) ? jfirst : ((e < end) ? col[e] : -1);
       const int cnt = min(U, end - eb);
       uint32_t xs[U];
       bool use[U];
@@ -142,8 +150,11 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
       obj.add(xi);
       if (obj.n == kFlushAt) obj.flush(cnt_obj);
     }
-    beg = nbeg;
-    end = nend;
+    beg = pbeg;
+    end = pend;
+    jfirst = njfirst;
+    pbeg = ppbeg;
+    pend = ppend;
   }
   if (active) {
     obj.flush(cnt_obj);
