@@ -88,6 +88,16 @@ typedef struct cpra_config {
   uint64_t seed;            /* parameter / embedding initialisation              */
   uint64_t mem_cap_bytes;   /* 0: none; else init fails with CPRA_ENOMEM when the
                                device workspace would exceed it                    */
+  float es_tol;             /* early stopping (Implementation paragraph): a step
+                               is stale when both the penalty-form loss
+                               sum_s (cost_s + lambda_s pen_s) and the annealing
+                               term gamma_t sum_s ann_s rose or changed by at
+                               most es_tol (absolute, FP64 sums over s in
+                               order); after es_patience consecutive stale
+                               steps the step that completes the run stops:
+                               it and every later cpra_step leave parameters
+                               and Adam state unchanged                      */
+  int32_t es_patience;      /* 0: no early stopping                             */
 } cpra_config;
 
 /* Result of rounding one shot (App. C.2) and evaluating it exactly. */
@@ -103,7 +113,7 @@ typedef struct cpra_ctx cpra_ctx;
 /* Fills *cfg with defaults: MIS, S = 8, H0 = H1 = 16, alpha = 2, FP32,
    recompute 0, train_embedding 1, keep_emb_grad 0, DIV_STD, nu = 0,
    gamma -2 -> 0.1 over 3000 steps, Adam lr 1e-3, betas (0.9, 0.999),
-   eps 1e-8, wd 0, seed 1. */
+   eps 1e-8, wd 0, seed 1, no early stopping (es_patience 0, es_tol 1e-5). */
 CPRA_API void cpra_config_default(cpra_config* cfg);
 
 /* Number of trainable GNN parameters excluding node embeddings:
@@ -170,9 +180,15 @@ CPRA_API cpra_status cpra_round_eval(cpra_ctx* ctx, cpra_shot_eval* out,
    steps and after the last, tracks per shot the best evaluation: MIS the
    largest objective with violations == 0 (objective -1 if none seen),
    MaxCut the largest cut.  best_out: host [S]; best_step_out: host [S] step
-   index of that evaluation (or -1), may be NULL. */
+   index of that evaluation (or -1), may be NULL.  With es_patience > 0 the
+   loop ends at the first evaluation after early stopping fired (the
+   parameters are frozen from the stopping step on). */
 CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every,
                        cpra_shot_eval* best_out, int64_t* best_step_out);
+
+/* Schedule index t of the cpra_step at which early stopping fired, or -1
+   (also when es_patience is 0).  Synchronises. */
+CPRA_API int64_t cpra_early_stop_step(cpra_ctx* ctx);
 
 /* Tensors a context exposes for checkpoints, tests and inspection. */
 enum {

@@ -299,6 +299,41 @@ def gamma_schedule(t, T, gamma0, gamma1):
     return gamma0 + (gamma1 - gamma0) * min(t, T - 1) / (T - 1)
 
 
+def early_stop_step(terms_seq, gammas, lam, problem, tol, patience):
+    """Early stopping of the Implementation paragraph: the run is monitored
+    through the summed penalty-form loss l_t = sum_s (cost_s + lambda_s pen_s)
+    (MaxCut: sum_s cost_s) and the annealing term phi_t = gamma_t sum_s ann_s,
+    with a tolerance and a patience.  Reading (the paper gives only the two
+    numbers): step t > 0 is stale when, for both monitored values, the change
+    from step t-1 is positive or at most `tol` in magnitude; the run stops at
+    the step that completes `patience` consecutive stale steps.  Sums run over
+    s = 0..S-1 in order, in float64, from the per-step terms as given.
+
+    terms_seq: per step (cost[S], pen[S], ann[S]); gammas: per step gamma_t.
+    Returns the index of the stopping step, or -1."""
+    prev = None
+    count = 0
+    for t, ((cost, pen, ann), gamma) in enumerate(zip(terms_seq, gammas)):
+        l_t = 0.0
+        a_t = 0.0
+        for s in range(len(cost)):
+            ls = float(cost[s])
+            if problem == MIS:
+                ls = ls + float(lam[s]) * float(pen[s])
+            l_t = l_t + ls
+            a_t = a_t + float(ann[s])
+        phi_t = float(gamma) * a_t
+        if prev is not None:
+            dl = l_t - prev[0]
+            dp = phi_t - prev[1]
+            stale = (dl > 0.0 or abs(dl) <= tol) and (dp > 0.0 or abs(dp) <= tol)
+            count = count + 1 if stale else 0
+            if count >= patience:
+                return t
+        prev = (l_t, phi_t)
+    return -1
+
+
 # --------------------------------------------------------------------------
 # rounding and integer evaluation (App. C.2, Table objective-functions)
 # --------------------------------------------------------------------------

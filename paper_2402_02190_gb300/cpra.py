@@ -33,7 +33,7 @@ ABI_FUNCTIONS = (
     "cpra_launch_count", "cpra_profile_enable", "cpra_profile_read", "cpra_kernel_name",
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
-    "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward",
+    "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
 )
 NOALLOC_MAX_S = 1024
 
@@ -53,6 +53,7 @@ class Config(C.Structure):
         ("gamma1", C.c_float), ("schedule_steps", C.c_int64), ("lr", C.c_float),
         ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
         ("weight_decay", C.c_float), ("seed", C.c_uint64), ("mem_cap_bytes", C.c_uint64),
+        ("es_tol", C.c_float), ("es_patience", C.c_int32),
     ]
 
 
@@ -94,6 +95,7 @@ def lib():
         "cpra_get_P": (C.c_int, [vp, vp]),
         "cpra_param_count": (i64, [vp]),
         "cpra_launch_count": (i64, [vp]),
+        "cpra_early_stop_step": (i64, [vp]),
         "cpra_profile_enable": (None, [vp, C.c_int]),
         "cpra_profile_read": (i32, [vp, vp, vp, i32]),
         "cpra_kernel_name": (C.c_char_p, [i32]),
@@ -282,6 +284,20 @@ def cpra_launch_count(ctx) -> int:
     return int(lib().cpra_launch_count(ctx))
 
 
+def cpra_early_stop_step(ctx) -> int:
+    return int(lib().cpra_early_stop_step(ctx))
+
+
+def paper_preset(problem: int, max_steps: int = 50_000) -> dict:
+    """Configuration keywords of the paper's experiments (Implementation
+    paragraph): AdamW lr 1e-4, weight decay 1e-2; gamma(0) = -20 for MIS and
+    -6 for MaxCut rising by 1e-3 per step (a linear schedule over max_steps);
+    alpha = 2; early stopping with tolerance 1e-5 and patience 1000."""
+    g0 = -20.0 if problem == MIS else -6.0
+    return dict(lr=1e-4, weight_decay=1e-2, gamma0=g0, gamma1=g0 + 1e-3 * (max_steps - 1),
+                schedule_steps=max_steps, alpha=2, es_tol=1e-5, es_patience=1000)
+
+
 def cpra_profile_enable(ctx, on: bool = True) -> None:
     lib().cpra_profile_enable(ctx, 1 if on else 0)
 
@@ -377,6 +393,9 @@ class Solver:
 
     def solve(self, steps: int, eval_every: int):
         return cpra_solve(self.ctx, steps, eval_every)
+
+    def early_stop_step(self) -> int:
+        return cpra_early_stop_step(self.ctx)
 
     def get(self, which: int) -> np.ndarray:
         return cpra_get_tensor(self.ctx, which)

@@ -118,6 +118,7 @@ struct cpra_ctx {
   void* GHM = nullptr;   // aliases HM when recompute
   void* GXM = nullptr;   // aliases XM when recompute
   uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
+  EarlyStopState* es = nullptr;   // early-stopping monitor (device)
   bool recompute = false;
   uint32_t* xbits = nullptr;
   float* loss_part = nullptr;
@@ -187,6 +188,8 @@ std::string validate_config(const cpra_config* cfg) {
   if (cfg->diversity_kind != CPRA_DIV_STD && cfg->diversity_kind != CPRA_DIV_VAR) return "bad diversity_kind";
   if (cfg->keep_emb_grad != 0 && cfg->keep_emb_grad != 1) return "keep_emb_grad must be 0 or 1";
   if (cfg->recompute != 0 && cfg->recompute != 1) return "recompute must be 0 or 1";
+  if (cfg->es_patience < 0 || !(cfg->es_tol >= 0.f) || !std::isfinite(cfg->es_tol))
+    return "early stopping needs es_patience >= 0 and a finite es_tol >= 0";
   if (cfg->problem == CPRA_MIS && cfg->lambda == nullptr) return "MIS needs lambda[S]";
   if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
   if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
@@ -269,6 +272,7 @@ size_t carve(cpra_ctx* c, void* base) {
   c->wg_part_floats = slab * (size_t)(4 * c->num_sms);
   c->wg_part = cv.take<float>(c->wg_part_floats);
   c->err_flag = cv.take<int>(4);
+  c->es = cv.take<EarlyStopState>(1);
   c->W1s = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W1t = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W2s = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
@@ -328,6 +332,25 @@ void refresh_shadows(cpra_ctx* c) {
 void refresh_emb_shadow(cpra_ctx* c) {
   copy_rows_launch(c->N, c->H0, c->X0m, c->XM, 2 * c->H0, c->act_dt, c->stream);
   c->launches += 1;
+}
+
+// Early-stopping state: reset, and read back (fixing the host's Adam step
+// count, which runs ahead of the device once the parameters froze).
+void reset_early_stop(cpra_ctx* c) {
+  EarlyStopState h{};
+  h.stop_step = -1;
+  cudaMemcpyAsync(c->es, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+}
+cpra_status read_early_stop(cpra_ctx* c, EarlyStopState* h) {
+  cudaError_t e = cudaMemcpyAsync(h, c->es, sizeof(*h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return CPRA_ECUDA;
+  if (h->stopped) c->opt_steps = h->updates_at_stop;
+  return CPRA_OK;
+}
+const int* halt_flag(const cpra_ctx* c) {
+  return c->cfg.es_patience > 0 ? &c->es->stopped : nullptr;
 }
 
 float gamma_at(const cpra_config& cfg, int64_t t) {
@@ -562,6 +585,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       a.Y = c->gX0; a.ldy = H0; a.mean = 0;
       if (fuse_adam) {
         a.adam = 1;
+        a.halt = halt_flag(c);
         if (!c->cfg.keep_emb_grad) a.Y = nullptr;
         a.emb = c->X0m; a.emb_m = c->X0_m; a.emb_v = c->X0_v;
         a.shadow = c->XM; a.lds = 2 * H0;
@@ -588,7 +612,7 @@ cpra_status run_update(cpra_ctx* c) {
   {
     Region r(c, K_ADAM);
     adam_launch(c->nparam, c->theta, c->theta_m, c->theta_v, c->grad, c->cfg.lr, c->cfg.beta1,
-                c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, c->stream);
+                c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, halt_flag(c), c->stream);
     c->launches += 1;
     refresh_shadows(c);
   }
@@ -642,6 +666,8 @@ void cpra_config_default(cpra_config* cfg) {
   cfg->weight_decay = 0.f;
   cfg->seed = 1;
   cfg->mem_cap_bytes = 0;
+  cfg->es_tol = 1e-5f;
+  cfg->es_patience = 0;
 }
 
 int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S) {
@@ -744,6 +770,7 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   cudaMemsetAsync(c->P, 0, sizeof(float) * N * c->S_pad, st);
   cudaMemsetAsync(c->GZ2, 0, act * N * c->S_pad, st);
   cudaMemsetAsync(c->err_flag, 0, sizeof(int) * 4, st);
+  reset_early_stop(c);
   cudaMemsetAsync(c->terms, 0, sizeof(float) * (4 * c->S + 1), st);
   // parameters: U(+-1/sqrt(fan_in)) for weights and biases, N(0,1) embeddings
   const Layout L = layout_of(c->H0, c->H1, c->S);
@@ -775,6 +802,12 @@ cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
   const float gamma = gamma_at(c->cfg, t);
   cpra_status s = run_forward_and_loss(c, gamma, true);
   if (s != CPRA_OK) return s;
+  if (c->cfg.es_patience > 0) {
+    early_stop_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S, gamma,
+                      c->cfg.es_tol, c->cfg.es_patience, (long long)t, (long long)c->opt_steps,
+                      c->es, c->stream);
+    c->launches += 1;
+  }
   const bool emb = c->cfg.train_embedding != 0;
   s = run_backward(c, emb, /*fuse_adam=*/emb);
   if (s != CPRA_OK) return s;
@@ -875,6 +908,12 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
           best_step[s] = t;
         }
       }
+      if (c->cfg.es_patience > 0) {
+        EarlyStopState h;
+        st = read_early_stop(c, &h);
+        if (st != CPRA_OK) return fail(c, st, "early-stopping state readback");
+        if (h.stopped) break;
+      }
     }
   }
   if (best_step_out) std::memcpy(best_step_out, best_step.data(), sizeof(int64_t) * c->S);
@@ -930,6 +969,10 @@ cpra_status cpra_get_tensor(cpra_ctx* c, int32_t which, void* host, size_t nbyte
   cpra_status s = CPRA_OK;
   if (which == CPRA_T_STEP) {
     s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+    if (s == CPRA_OK && c->cfg.es_patience > 0) {
+      EarlyStopState h;
+      s = read_early_stop(c, &h);
+    }
     std::memcpy(host, &c->opt_steps, sizeof(int64_t));
     return s;
   }
@@ -990,18 +1033,23 @@ cpra_status cpra_get_state(cpra_ctx* c, void* buf, size_t* nbytes) {
   if (!c || !nbytes) return CPRA_EINVAL;
   const size_t tb = (size_t)c->nparam * sizeof(float);
   const size_t eb = (size_t)c->N * c->H0 * sizeof(float);
-  const size_t total = sizeof(StateHeader) + 3 * tb + 3 * eb;
+  const size_t total = sizeof(StateHeader) + sizeof(EarlyStopState) + 3 * tb + 3 * eb;
   if (!buf) { *nbytes = total; return CPRA_OK; }
   if (*nbytes < total) return fail(c, CPRA_EINVAL, "state buffer too small");
   StateHeader h{};
   std::memcpy(h.magic, "CPRAST01", 8);
-  h.version = 1; h.N = c->N; h.H0 = c->H0; h.H1 = c->H1; h.S = c->S; h.nparam = c->nparam;
+  h.version = 2; h.N = c->N; h.H0 = c->H0; h.H1 = c->H1; h.S = c->S; h.nparam = c->nparam;
   cpra_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
   if (s != CPRA_OK) return s;
+  EarlyStopState es;
+  s = read_early_stop(c, &es);
+  if (s != CPRA_OK) return fail(c, s, "early-stopping state readback");
   h.opt_steps = c->opt_steps;
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
+  std::memcpy(p, &es, sizeof(es));
+  p += sizeof(es);
   const int32_t ids[6] = {CPRA_T_THETA, CPRA_T_THETA_M, CPRA_T_THETA_V,
                           CPRA_T_EMB, CPRA_T_EMB_M, CPRA_T_EMB_V};
   for (int k = 0; k < 6; ++k) {
@@ -1018,14 +1066,21 @@ cpra_status cpra_set_state(cpra_ctx* c, const void* buf, size_t nbytes) {
   if (!c || !buf) return CPRA_EINVAL;
   const size_t tb = (size_t)c->nparam * sizeof(float);
   const size_t eb = (size_t)c->N * c->H0 * sizeof(float);
-  const size_t total = sizeof(StateHeader) + 3 * tb + 3 * eb;
+  const size_t total = sizeof(StateHeader) + sizeof(EarlyStopState) + 3 * tb + 3 * eb;
   if (nbytes != total) return fail(c, CPRA_ESTATE, "state blob has the wrong size");
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  if (std::memcmp(h.magic, "CPRAST01", 8) != 0 || h.version != 1 || h.N != c->N ||
+  if (std::memcmp(h.magic, "CPRAST01", 8) != 0 || h.version != 2 || h.N != c->N ||
       h.H0 != c->H0 || h.H1 != c->H1 || h.S != c->S || h.nparam != c->nparam)
     return fail(c, CPRA_ESTATE, "state blob does not match this context");
   const char* p = static_cast<const char*>(buf) + sizeof(h);
+  EarlyStopState es;
+  std::memcpy(&es, p, sizeof(es));
+  p += sizeof(es);
+  cpra_status se = cuda_check(c, cudaMemcpyAsync(c->es, &es, sizeof(es), cudaMemcpyHostToDevice,
+                                                 c->stream), "early-stopping state");
+  if (se == CPRA_OK) se = cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+  if (se != CPRA_OK) return se;
   const int32_t ids[6] = {CPRA_T_THETA, CPRA_T_THETA_M, CPRA_T_THETA_V,
                           CPRA_T_EMB, CPRA_T_EMB_M, CPRA_T_EMB_V};
   for (int k = 0; k < 6; ++k) {
@@ -1045,6 +1100,13 @@ cpra_status cpra_get_P(cpra_ctx* c, float* host_NxS) {
 
 int64_t cpra_param_count(const cpra_ctx* c) { return c ? c->nparam : 0; }
 int64_t cpra_launch_count(const cpra_ctx* c) { return c ? c->launches : 0; }
+
+int64_t cpra_early_stop_step(cpra_ctx* c) {
+  if (!c || c->cfg.es_patience <= 0) return -1;
+  EarlyStopState h;
+  if (read_early_stop(c, &h) != CPRA_OK) return -1;
+  return h.stopped ? (int64_t)h.stop_step : -1;
+}
 
 void cpra_profile_enable(cpra_ctx* c, int on) {
   if (!c) return;

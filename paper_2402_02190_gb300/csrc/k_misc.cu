@@ -10,7 +10,9 @@ namespace {
 
 __global__ void adam_kernel(int64_t n, float* __restrict__ th, float* __restrict__ m,
                             float* __restrict__ v, const float* __restrict__ g, float lr,
-                            float b1, float b2, float eps, float wd, float bc1, float bc2) {
+                            float b1, float b2, float eps, float wd, float bc1, float bc2,
+                            const int* halt) {
+  if (halt && *halt) return;  // early stopping froze the parameters
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float mi = m[i], vi = v[i];
@@ -130,9 +132,48 @@ inline unsigned grid_for(int64_t n) {
 
 void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g, float lr,
                  float beta1, float beta2, float eps, float wd, float bc1, float bc2,
-                 cudaStream_t st) {
+                 const int* halt, cudaStream_t st) {
   adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, m, v, g, lr, beta1, beta2, eps, wd, bc1,
-                                           bc2);
+                                           bc2, halt);
+}
+
+namespace {
+
+// Single thread: the sums run in a fixed order with explicit roundings (no
+// contraction into fused multiply-adds), so the decision is reproducible.
+__global__ void early_stop_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
+                                  int S, float gamma, float tol, int patience, long long t,
+                                  long long updates, EarlyStopState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || st->stopped) return;
+  double l = 0.0, ann = 0.0;
+  for (int s = 0; s < S; ++s) {
+    double ls = (double)terms[s];
+    if (lambda) ls = __dadd_rn(ls, __dmul_rn((double)lambda[s], (double)terms[S + s]));
+    l = __dadd_rn(l, ls);
+    ann = __dadd_rn(ann, (double)terms[2 * S + s]);
+  }
+  const double phi = __dmul_rn((double)gamma, ann);
+  if (st->have_prev) {
+    const double dl = __dadd_rn(l, -st->prev_l), dp = __dadd_rn(phi, -st->prev_phi);
+    const bool stale = (dl > 0.0 || fabs(dl) <= (double)tol) && (dp > 0.0 || fabs(dp) <= (double)tol);
+    st->count = stale ? st->count + 1 : 0;
+    if (st->count >= patience) {
+      st->stopped = 1;
+      st->stop_step = t;
+      st->updates_at_stop = updates;
+    }
+  }
+  st->prev_l = l;
+  st->prev_phi = phi;
+  st->have_prev = 1;
+}
+
+}  // namespace
+
+void early_stop_launch(const float* terms, const float* lambda, int S, float gamma, float tol,
+                       int patience, long long t, long long updates, EarlyStopState* st,
+                       cudaStream_t stream) {
+  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, gamma, tol, patience, t, updates, st);
 }
 
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd, int ddst,

@@ -50,6 +50,8 @@ spmm_rows_kernel(SpmmArgs a) {
   const TX* ADD = static_cast<const TX*>(a.add);  // may alias Y (same row, read first)
   const TX* __restrict__ MASK = static_cast<const TX*>(a.mask);
   const uint64_t pol = l2_evict_first_policy();
+  bool update = true;  // embedding Adam step (ADAM kind), off once early stopping fired
+  if constexpr (ADAM) update = !(a.halt && *a.halt);
 
   float csum[CPL][VEC];
 #pragma unroll
@@ -176,7 +178,8 @@ spmm_rows_kernel(SpmmArgs a) {
       }
       if constexpr (ADAM) {
         // o is dR/dh^0 for this chunk: one Adam step on the FP32 master row,
-        // its moments, and the activation-dtype copy the forward reads
+        // its moments, and the activation-dtype copy the forward reads (the
+        // copy is rewritten even when early stopping froze the update)
         const int64_t off = i * a.H + ch * VEC;
         float th[VEC], m[VEC], vv[VEC];
 #pragma unroll
@@ -186,13 +189,15 @@ spmm_rows_kernel(SpmmArgs a) {
           widen(ld_stream16(a.emb_v + off + q, pol), vv + q, (const float*)nullptr);
         }
         if (Y) storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);
+        if (update) {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v)
-          th[v] = adam_update(th[v], m[v], vv[v], o[v], a.lr, a.beta1, a.beta2, a.eps, a.wd,
-                              a.bc1, a.bc2);
-        storeN_stream<VEC>(a.emb + off, th, pol);
-        storeN_stream<VEC>(a.emb_m + off, m, pol);
-        storeN_stream<VEC>(a.emb_v + off, vv, pol);
+          for (int v = 0; v < VEC; ++v)
+            th[v] = adam_update(th[v], m[v], vv[v], o[v], a.lr, a.beta1, a.beta2, a.eps, a.wd,
+                                a.bc1, a.bc2);
+          storeN_stream<VEC>(a.emb + off, th, pol);
+          storeN_stream<VEC>(a.emb_m + off, m, pol);
+          storeN_stream<VEC>(a.emb_v + off, vv, pol);
+        }
         storeN_stream<VEC>(static_cast<TX*>(a.shadow) + i * a.lds + ch * VEC, th, pol);
       } else {
         storeN_stream<VEC>(Y + i * a.ldy + ch * VEC, o, pol);

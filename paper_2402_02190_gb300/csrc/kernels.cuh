@@ -44,6 +44,7 @@ struct SpmmArgs {
   // ([N x H] f32, row stride H) and writes the updated row to shadow (dtype
   // dx, row stride lds).  Y may be null (the gradient is then not stored).
   int adam = 0;
+  const int* halt = nullptr;  // while *halt != 0 the embedding rows are left as they are
   float* emb = nullptr;
   float* emb_m = nullptr;
   float* emb_v = nullptr;
@@ -150,9 +151,31 @@ void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp,
                    float* out, int64_t ldo, cudaStream_t st);
 
 // ---------------------------------------------------------------- misc
+// Adam on n parameters; skipped entirely while *halt != 0 (halt may be null).
 void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g,
                  float lr, float beta1, float beta2, float eps, float wd,
-                 float bc1, float bc2, cudaStream_t st);
+                 float bc1, float bc2, const int* halt, cudaStream_t st);
+
+// Early-stopping monitor (Implementation paragraph), one thread: from the
+// step's loss terms (cost S | pen S | ann S) forms l = sum_s (cost_s +
+// lambda_s pen_s) (lambda null: cost only) and phi = gamma * sum_s ann_s in
+// FP64 in the order s = 0..S-1; a step is stale when for both values the
+// change from the previous step is > 0 or |change| <= tol; after `patience`
+// consecutive stale steps sets `stopped`, stop_step = t and
+// updates_at_stop = the Adam updates applied so far.  Does nothing once
+// stopped.
+struct EarlyStopState {
+  double prev_l, prev_phi;
+  long long stop_step;        // -1 while running
+  long long updates_at_stop;
+  int count;                  // consecutive stale steps
+  int have_prev;
+  int stopped;                // halts the parameter updates
+  int pad;
+};
+void early_stop_launch(const float* terms, const float* lambda, int S, float gamma, float tol,
+                       int patience, long long t, long long updates, EarlyStopState* st,
+                       cudaStream_t stream);
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd,
                       int ddst, cudaStream_t st);
 // BF16 shadows of the dense weights:

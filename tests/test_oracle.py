@@ -330,6 +330,71 @@ def test_gamma_schedule_endpoints():
     assert O.gamma_schedule(1500, 3001, -2.0, 0.1) == pytest.approx(-0.95)
 
 
+# ------------------------------------------------------ early stopping
+def _es_terms(ls, phis, S=3, lam=(1.0, 2.0, 0.5)):
+    """Per-step terms whose monitored sums are exactly ls[t] and phis[t]
+    (gamma_t = 1): cost carries l_t in shot 0, pen = 0, ann carries phi_t."""
+    seq = []
+    for l_t, p_t in zip(ls, phis):
+        cost = np.zeros(S); pen = np.zeros(S); ann = np.zeros(S)
+        cost[0] = l_t
+        ann[0] = p_t
+        seq.append((cost, pen, ann))
+    return seq, [1.0] * len(ls), np.array(lam)
+
+
+def test_early_stop_constant_run_stops_after_patience():
+    seq, g, lam = _es_terms([5.0] * 10, [2.0] * 10)
+    # steps 1, 2, 3 are stale: patience 3 completes at step 3
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 3) == 3
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 9) == 9
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 10) == -1
+
+
+def test_early_stop_needs_both_values_stale():
+    # the loss keeps falling by more than tol while phi is flat: never stale
+    ls = [10.0 - t for t in range(12)]
+    seq, g, lam = _es_terms(ls, [1.0] * 12)
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 2) == -1
+    # and the other way round
+    seq, g, lam = _es_terms([1.0] * 12, ls)
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 2) == -1
+
+
+def test_early_stop_rise_counts_and_improvement_resets():
+    # rises count as stale; a drop larger than tol resets the count
+    ls = [5.0, 5.5, 6.0, 4.0, 4.0 + 5e-6, 4.0 + 1e-5, 4.1]
+    seq, g, lam = _es_terms(ls, [0.0] * len(ls))
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 2) == 2
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 3) == 6
+    assert O.early_stop_step(seq, g, lam, O.MIS, 1e-5, 4) == -1
+    # a drop of exactly tol is still stale (|change| <= tol)
+    seq, g, lam = _es_terms([1.0, 1.0 - 2.0 ** -20, 1.0 - 2.0 ** -19], [0.0] * 3)
+    assert O.early_stop_step(seq, g, lam, O.MIS, 2.0 ** -20, 2) == 2
+
+
+def test_early_stop_monitored_sums():
+    """The penalty weights enter the MIS loss and not the MaxCut one, and
+    gamma scales the annealing term."""
+    S = 3
+    lam = np.array([1.0, 2.0, 0.5])
+    cost = np.array([-1.0, -2.0, -3.0])
+    pen = np.array([0.5, 0.25, 1.0])
+    ann = np.array([1.0, 2.0, 3.0])
+    # MIS: l = -6 + (0.5 + 0.5 + 0.5) = -4.5; an identical second step is stale
+    seq = [(cost, pen, ann), (cost, pen, ann)]
+    assert O.early_stop_step(seq, [1.0, 1.0], lam, O.MIS, 0.0, 1) == 1
+    # the pen entries change by +1 in step 2: MIS loss rises (stale), MaxCut
+    # loss is unchanged (stale); phi falls by 6 with gamma 1 -> not stale
+    seq = [(cost, pen, ann), (cost, pen + 1.0, ann)]
+    assert O.early_stop_step(seq, [1.0, -1.0], lam, O.MIS, 1e-5, 1) == -1
+    assert O.early_stop_step(seq, [1.0, 1.0], lam, O.MIS, 1e-5, 1) == 1
+    # MIS loss falls when pen falls; MaxCut ignores pen
+    seq = [(cost, pen, ann), (cost, pen - 0.25, ann)]
+    assert O.early_stop_step(seq, [1.0, 1.0], lam, O.MIS, 1e-5, 1) == -1
+    assert O.early_stop_step(seq, [1.0, 1.0], lam, O.MAXCUT, 1e-5, 1) == 1
+
+
 # ------------------------------------------------------ integer evaluation
 @pytest.mark.parametrize("seed", [0, 1])
 def test_integer_eval_invariants(seed):
