@@ -115,6 +115,22 @@ def ncu_traffic(kernel: str, workload: str):
         return None
 
 
+def max_over_ranks(x: float, dist_mod=None, device="cuda") -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if dist_mod is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job rate of `world` independent replicas that each processed
+    units_per_rank units, timed by the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -270,10 +286,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     prof = cpra.cpra_profile_read(solver.ctx)
     launches = solver.launches - launches0
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     solver.close()
     del solver
     torch.cuda.synchronize()
@@ -290,10 +303,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     s2.close()
+    if dist:
+        dist.barrier()
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = (8 * (N + 1) + 4 * nnz + (4 * S if lam is not None else 0)) / args.steps
     d2h = (3 * S + 1) * 4 + (S * 24 + 8) / args.steps
 
-    value = world * nnz * S * args.steps / (ms / 1e3)
+    value = replica_throughput(world, nnz * S * args.steps, ms / 1e3)
     peak, peak_src = read_peaks()
     loss_ms, loss_n = prof.get("loss_fused", (0.0, 0))
     g_bytes = 2 if w["precision"] == 1 else 4
@@ -319,7 +335,7 @@ def run_gpu(args):
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "alg_bytes_per_launch": alg, "avg_ms": loss_ms / loss_n if loss_n else None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
-        "e2e": {"value": nnz * S * args.steps / e2e_s, "unit": METRIC,
+        "e2e": {"value": replica_throughput(world, nnz * S * args.steps, e2e_s), "unit": METRIC,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "seconds": e2e_s},
         "gpu_launches": launches,
