@@ -190,6 +190,20 @@ CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every
    (also when es_patience is 0).  Synchronises. */
 CPRA_API int64_t cpra_early_stop_step(cpra_ctx* ctx);
 
+/* Warm start: a fixed per-node, per-shot offset L0 added to the head's
+   pre-activation, Z2 = [H1|M2] Wcat2^T + b2 + L0, so that P = sigma(Z2)
+   starts near sigma(L0) while the GCN output is small; the paper's
+   neighbourhood of this idea is its meta-learned initialisation and
+   two-stage training (Related work; App. C.4).  logits: float [N x ld]
+   (ld >= S), row-major, on the host (on_device = 0) or the current device
+   (on_device = 1); the library keeps a copy in the dense layers' dtype
+   (bfloat16 in the BF16 form) in device memory it allocates itself
+   (N x round_up(S,16) values, counted against mem_cap_bytes, freed by
+   cpra_destroy).  NULL removes the offset.  Synchronises.  Errors:
+   CPRA_EINVAL (ld < S), CPRA_ENOMEM. */
+CPRA_API cpra_status cpra_set_init_logits(cpra_ctx* ctx, const float* logits, int64_t ld,
+                                          int32_t on_device);
+
 /* Tensors a context exposes for checkpoints, tests and inspection. */
 enum {
   CPRA_T_THETA = 0,     /* float [param_count] flat: Wcat1=[B1|W1] (H1 x 2H0),
@@ -331,6 +345,66 @@ CPRA_API cpra_status cpra_op_loss_noalloc(int64_t N, int32_t S, const int32_t* r
                                           float gamma, float nu, int32_t diversity_kind,
                                           int32_t grad_kind, float* G, int64_t ldg,
                                           uint32_t* x_bits, float* terms, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Warm-start network.  A three-layer GCN with the layer of Eq. GCN (self
+ * weight B, neighbour weight W on the row-mean aggregate, bias; ReLU after
+ * layers 1 and 2) maps fixed node features (1, deg/8 and F-2 standard
+ * normal draws per node from a seeded counter-based stream) to S logits per
+ * node.  It is trained with the mean binary cross-entropy against rounded
+ * CPRA solutions x_is, and its logits seed a CPRA run through
+ * cpra_set_init_logits.  The paper has no such network; its nearest ideas
+ * are the meta-learned initialisation and the two-stage (S' -> S) training
+ * it discusses.  Graph arguments are DEVICE pointers: rowptr int32 [N+1],
+ * col int32 [nnz] (symmetric CSR, the layout of cpra_init_graph),
+ * features float [N x F], target bits uint32 [N x ceil(S/32)] with bit
+ * (s mod 32) of word s/32 = x_is (cpra_round_eval's layout), logits float
+ * [N x ld].  All calls are ordered on the network's stream.
+ * ------------------------------------------------------------------------ */
+typedef struct cpra_ws cpra_ws;
+typedef struct cpra_ws_config {
+  int32_t F;           /* feature width, multiple of 16, >= 16             */
+  int32_t H;           /* hidden width, multiple of 16                     */
+  int32_t S;           /* logits per node (shots), 1..1024                 */
+  int32_t precision;   /* CPRA_FP32 or CPRA_BF16 (dense layers)            */
+  float lr, beta1, beta2, eps, weight_decay;   /* Adam / AdamW            */
+  uint64_t seed;       /* parameter initialisation                         */
+} cpra_ws_config;
+
+/* F = 16, H = 64, S = 32, BF16, Adam lr 1e-3 (0.9, 0.999, 1e-8), wd 0, seed 1. */
+CPRA_API void cpra_ws_config_default(cpra_ws_config* cfg);
+/* Flat parameter layout: Wcat1 = [B1|W1] (H x 2F), b1 (H), Wcat2 (H x 2H),
+   b2 (H), Wcat3 (S x 2H), b3 (S); 0 for an invalid configuration. */
+CPRA_API int64_t cpra_ws_param_count(const cpra_ws_config* cfg);
+/* Creates a network for graphs of up to max_nodes nodes and max_nnz CSR
+   entries (its activations are sized for them and allocated by the
+   library).  Parameters: U(+-1/sqrt(fan_in)) from cfg->seed.  Errors:
+   CPRA_EINVAL, CPRA_ENOMEM, CPRA_ECUDA. */
+CPRA_API cpra_status cpra_ws_create(cpra_ws** out, const cpra_ws_config* cfg, int64_t max_nodes,
+                                    int64_t max_nnz, void* cuda_stream);
+/* Writes the node features of a graph (see above) to features [N x F]. */
+CPRA_API cpra_status cpra_ws_features(cpra_ws* ws, int64_t N, const int32_t* rowptr,
+                                      uint64_t graph_seed, float* features);
+/* One training step on one graph (or a disjoint union of graphs): forward,
+   mean binary cross-entropy over the N x S logits, hand-written adjoint,
+   Adam.  loss_out: host float receiving the loss, or NULL (then no
+   synchronisation).  Errors: CPRA_EINVAL (N or nnz above the sizes given at
+   creation), CPRA_ECUDA, CPRA_ETIMEOUT. */
+CPRA_API cpra_status cpra_ws_train_step(cpra_ws* ws, int64_t N, int64_t nnz,
+                                        const int32_t* rowptr, const int32_t* col,
+                                        const float* features, const uint32_t* target_bits,
+                                        float* loss_out);
+/* Forward only: logits [N x ld] (ld >= S).  Graphs larger than the sizes
+   given at creation are processed in node order through the same buffers
+   only if they fit; otherwise CPRA_EINVAL. */
+CPRA_API cpra_status cpra_ws_predict(cpra_ws* ws, int64_t N, int64_t nnz, const int32_t* rowptr,
+                                     const int32_t* col, const float* features, float* logits,
+                                     int64_t ld);
+/* Host copies of the flat parameters (float [cpra_ws_param_count]); gradient
+   of the last training step with which = 1.  Synchronise. */
+CPRA_API cpra_status cpra_ws_get_params(cpra_ws* ws, int32_t which, float* host, size_t count);
+CPRA_API cpra_status cpra_ws_set_params(cpra_ws* ws, const float* host, size_t count);
+CPRA_API void cpra_ws_destroy(cpra_ws* ws);
 
 #ifdef __cplusplus
 }

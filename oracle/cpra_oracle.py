@@ -145,11 +145,14 @@ def bf16_round(x) -> np.ndarray:
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(g: Graph, theta, X0, H0, H1, S, relu_decision=None):
+def forward(g: Graph, theta, X0, H0, H1, S, relu_decision=None, init_logits=None):
     """relu_decision: None decides the ReLU sign 1[Z1 > 0] on the float64
     Z1; "bf16" decides it on Z1 recomputed from bfloat16-rounded operands
     (X0, the neighbour mean and the weights), the precision in which the
-    BF16 form's kernels take that decision.  All values stay float64."""
+    BF16 form's kernels take that decision.  All values stay float64.
+    init_logits: optional N x S warm-start offset L0 added to the head's
+    pre-activation (Z2 = ... + b2 + L0); constant, so the gradient formulas
+    are unchanged."""
     p = unpack(theta, H0, H1, S)
     X0 = np.asarray(X0, dtype=np.float64)
     M1 = mean_aggregate(g, X0)
@@ -166,6 +169,8 @@ def forward(g: Graph, theta, X0, H0, H1, S, relu_decision=None):
     H1a = np.where(on, Z1, 0.0)
     M2 = mean_aggregate(g, H1a)
     Z2 = H1a @ p["B2"].T + M2 @ p["W2"].T + p["b2"]
+    if init_logits is not None:
+        Z2 = Z2 + np.asarray(init_logits, dtype=np.float64)
     P = sigmoid(Z2)
     return dict(X0=X0, M1=M1, Z1=Z1, relu_on=on, H1=H1a, M2=M2, Z2=Z2, P=P)
 
@@ -385,7 +390,7 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
     lr, beta1, beta2, eps, wd, train_embedding.
     adam_state: dict(m_theta, v_theta, m_X0, v_X0) or None (zeros)."""
     H0, H1, S = cfg["H0"], cfg["H1"], cfg["S"]
-    cache = forward(g, theta, X0, H0, H1, S, cfg.get("relu_decision"))
+    cache = forward(g, theta, X0, H0, H1, S, cfg.get("relu_decision"), cfg.get("init_logits"))
     P = cache["P"]
     terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"])
     L = total_loss(terms, cfg["lam"], cfg["gamma"], cfg["nu"], cfg["problem"])

@@ -34,6 +34,9 @@ ABI_FUNCTIONS = (
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
     "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
+    "cpra_set_init_logits", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
+    "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
+    "cpra_ws_set_params", "cpra_ws_destroy",
 )
 NOALLOC_MAX_S = 1024
 
@@ -54,6 +57,14 @@ class Config(C.Structure):
         ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
         ("weight_decay", C.c_float), ("seed", C.c_uint64), ("mem_cap_bytes", C.c_uint64),
         ("es_tol", C.c_float), ("es_patience", C.c_int32),
+    ]
+
+
+class WsConfig(C.Structure):
+    _fields_ = [
+        ("F", C.c_int32), ("H", C.c_int32), ("S", C.c_int32), ("precision", C.c_int32),
+        ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+        ("weight_decay", C.c_float), ("seed", C.c_uint64),
     ]
 
 
@@ -96,12 +107,22 @@ def lib():
         "cpra_param_count": (i64, [vp]),
         "cpra_launch_count": (i64, [vp]),
         "cpra_early_stop_step": (i64, [vp]),
+        "cpra_set_init_logits": (i32, [vp, vp, i64, i32]),
         "cpra_profile_enable": (None, [vp, C.c_int]),
         "cpra_profile_read": (i32, [vp, vp, vp, i32]),
         "cpra_kernel_name": (C.c_char_p, [i32]),
         "cpra_last_error": (C.c_char_p, [vp]),
         "cpra_status_string": (C.c_char_p, [C.c_int]),
         "cpra_destroy": (None, [vp]),
+        "cpra_ws_config_default": (None, [vp]),
+        "cpra_ws_param_count": (i64, [vp]),
+        "cpra_ws_create": (i32, [vp, vp, i64, i64, vp]),
+        "cpra_ws_features": (i32, [vp, i64, vp, C.c_uint64, vp]),
+        "cpra_ws_train_step": (i32, [vp, i64, i64, vp, vp, vp, vp, vp]),
+        "cpra_ws_predict": (i32, [vp, i64, i64, vp, vp, vp, vp, i64]),
+        "cpra_ws_get_params": (i32, [vp, i32, vp, sz]),
+        "cpra_ws_set_params": (i32, [vp, vp, sz]),
+        "cpra_ws_destroy": (None, [vp]),
         "cpra_op_loss_scratch_bytes": (sz, [i64, i32]),
         "cpra_op_loss": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, i32, f32, f32, i32, i32,
                                    vp, i64, vp, vp, vp, sz, vp]),
@@ -288,6 +309,19 @@ def cpra_early_stop_step(ctx) -> int:
     return int(lib().cpra_early_stop_step(ctx))
 
 
+def cpra_set_init_logits(ctx, logits) -> None:
+    """logits: None, a host array [N, S] or a CUDA tensor [N, S] (float32)."""
+    if logits is None:
+        _check(lib().cpra_set_init_logits(ctx, None, 0, 0), ctx)
+        return
+    if hasattr(logits, "is_cuda") and logits.is_cuda:
+        t = logits.float().contiguous()
+        _check(lib().cpra_set_init_logits(ctx, C.c_void_p(t.data_ptr()), t.shape[1], 1), ctx)
+        return
+    a = np.ascontiguousarray(logits, dtype=np.float32)
+    _check(lib().cpra_set_init_logits(ctx, _ptr(a), a.shape[1], 0), ctx)
+
+
 def paper_preset(problem: int, max_steps: int = 50_000) -> dict:
     """Configuration keywords of the paper's experiments (Implementation
     paragraph): AdamW lr 1e-4, weight decay 1e-2; gamma(0) = -20 for MIS and
@@ -397,6 +431,13 @@ class Solver:
     def early_stop_step(self) -> int:
         return cpra_early_stop_step(self.ctx)
 
+    def set_init_logits(self, logits) -> None:
+        if hasattr(logits, "is_cuda") and logits.is_cuda:
+            import torch
+            # the copy runs on the solver's stream: order it after the producer
+            self.stream.wait_stream(torch.cuda.current_stream())
+        cpra_set_init_logits(self.ctx, logits)
+
     def get(self, which: int) -> np.ndarray:
         return cpra_get_tensor(self.ctx, which)
 
@@ -425,3 +466,100 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ warm start
+def ws_config(**kw) -> WsConfig:
+    cfg = WsConfig()
+    lib().cpra_ws_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def cpra_ws_param_count(cfg: WsConfig) -> int:
+    return int(lib().cpra_ws_param_count(C.byref(cfg)))
+
+
+class WarmStartNet:
+    """The warm-start network of the C ABI (cpra_ws_*).  Graph tensors are
+    CUDA tensors: rowptr/col int32, features float32 [N, F], target bits
+    uint32 stored as int32 [N, ceil(S/32)]."""
+
+    def __init__(self, max_nodes: int, max_nnz: int, stream=None, **cfg_kw):
+        import torch
+        self.cfg = ws_config(**cfg_kw)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        st = lib().cpra_ws_create(C.byref(h), C.byref(self.cfg), int(max_nodes), int(max_nnz),
+                                  C.c_void_p(self.stream.cuda_stream))
+        if st != CPRA_OK:
+            raise CpraError(st, f"cpra_ws_create failed ({st})")
+        self.ws = h
+        self.nparam = cpra_ws_param_count(self.cfg)
+
+    def _wait(self):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    @staticmethod
+    def _p(t):
+        return C.c_void_p(t.data_ptr())
+
+    def features(self, rowptr, graph_seed: int):
+        import torch
+        self._wait()
+        N = rowptr.numel() - 1
+        out = torch.empty((N, self.cfg.F), dtype=torch.float32, device=rowptr.device)
+        _check(lib().cpra_ws_features(self.ws, N, self._p(rowptr), C.c_uint64(graph_seed),
+                                      self._p(out)))
+        out.record_stream(self.stream)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
+    def train_step(self, rowptr, col, features, target_bits, want_loss: bool = True):
+        import torch
+        self._wait()
+        loss = C.c_float(0.0)
+        _check(lib().cpra_ws_train_step(self.ws, rowptr.numel() - 1, col.numel(), self._p(rowptr),
+                                        self._p(col), self._p(features), self._p(target_bits),
+                                        C.byref(loss) if want_loss else None))
+        for t in (rowptr, col, features, target_bits):
+            t.record_stream(self.stream)
+        return float(loss.value) if want_loss else None
+
+    def predict(self, rowptr, col, features):
+        import torch
+        self._wait()
+        N = rowptr.numel() - 1
+        S = self.cfg.S
+        ld = (S + 3) // 4 * 4
+        out = torch.empty((N, ld), dtype=torch.float32, device=rowptr.device)
+        _check(lib().cpra_ws_predict(self.ws, N, col.numel(), self._p(rowptr), self._p(col),
+                                     self._p(features), self._p(out), ld))
+        out.record_stream(self.stream)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return out[:, :S]
+
+    def params(self, which: int = 0) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().cpra_ws_get_params(self.ws, which, _ptr(out), out.size))
+        return out
+
+    def set_params(self, theta) -> None:
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().cpra_ws_set_params(self.ws, _ptr(a), a.size))
+
+    def close(self) -> None:
+        if self.ws:
+            lib().cpra_ws_destroy(self.ws)
+            self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -169,6 +169,26 @@ __device__ __forceinline__ float adam_update(float th, float& m, float& v, float
   return th - lr * mhat / (sqrtf(vhat) + eps);
 }
 
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+// Uniform [0, 1) with 24 random bits from stream (seed, tag) at index idx.
+__device__ __forceinline__ float u24(uint64_t seed, uint64_t tag, uint64_t idx) {
+  const uint64_t h = splitmix64(seed ^ splitmix64(tag) ^ (idx * 0xD1B54A32D192ED03ull));
+  return (float)(h >> 40) * (1.0f / 16777216.0f);  // [0, 1)
+}
+
+// A standard normal from two uniforms of the same stream (Box-Muller).
+__device__ __forceinline__ float normal_at(uint64_t seed, uint64_t tag, uint64_t i) {
+  const float u1 = u24(seed, tag, 2 * i) + (0.5f / 16777216.0f);
+  const float u2 = u24(seed, tag, 2 * i + 1);
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
 // Sum over the lanes of an aligned power-of-two segment of width W.
 template <int W>
 __device__ __forceinline__ float seg_sum(float v, unsigned mask) {

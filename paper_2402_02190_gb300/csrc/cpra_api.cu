@@ -119,6 +119,7 @@ struct cpra_ctx {
   void* GXM = nullptr;   // aliases XM when recompute
   uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
   EarlyStopState* es = nullptr;   // early-stopping monitor (device)
+  void* init_logits = nullptr;    // warm start: N x S_pad act dtype, own cudaMalloc
   bool recompute = false;
   uint32_t* xbits = nullptr;
   float* loss_part = nullptr;
@@ -458,6 +459,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
     g.ldb = 2 * H1; g.b_kmajor = 1;
     g.epi = EPI_BIAS_SIGMOID; g.bias = c->theta + L.b2;
     g.out0 = c->P; g.ld0 = c->S_pad; g.d0 = DT_F32; g.n_valid = c->S;
+    if (c->init_logits) { g.addend = c->init_logits; g.ld_add = c->S_pad; g.d_add = c->act_dt; }
     dense(c, g);
   }
   int grid = 0;
@@ -1171,8 +1173,54 @@ void cpra_destroy(cpra_ctx* c) {
     if (r.b) cudaEventDestroy(r.b);
   }
   if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+cpra_status cpra_set_init_logits(cpra_ctx* c, const float* logits, int64_t ld, int32_t on_device) {
+  if (!c) return CPRA_EINVAL;
+  cudaStream_t st = c->stream;
+  c->fwd_valid = false;
+  c->have_eval = false;
+  if (!logits) {  // back to the plain network
+    cpra_status s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+    if (c->init_logits) cudaFree(c->init_logits);
+    c->init_logits = nullptr;
+    return s;
+  }
+  if (ld < c->S) return fail(c, CPRA_EINVAL, "cpra_set_init_logits: ld < S");
+  const size_t act = c->act_dt == DT_BF16 ? 2 : 4;
+  const size_t bytes = (size_t)c->N * c->S_pad * act;
+  if (!c->init_logits) {
+    if (c->cfg.mem_cap_bytes && c->ws_bytes + bytes > c->cfg.mem_cap_bytes)
+      return fail(c, CPRA_ENOMEM, "cpra_set_init_logits: exceeds mem_cap_bytes");
+    if (cudaMalloc(&c->init_logits, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->init_logits = nullptr;
+      return fail(c, CPRA_ENOMEM, "cpra_set_init_logits: device allocation failed");
+    }
+  }
+  // stage as contiguous FP32 [N x S] on the device, then convert into the
+  // padded activation-dtype buffer (pad columns 0)
+  float* tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(float) * (size_t)c->N * c->S) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CPRA_ENOMEM, "cpra_set_init_logits: staging allocation failed");
+  }
+  cpra_status s = cuda_check(
+      c, cudaMemcpy2DAsync(tmp, sizeof(float) * c->S, logits, sizeof(float) * ld,
+                           sizeof(float) * c->S, c->N,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+      "init logits");
+  if (s == CPRA_OK) s = cuda_check(c, cudaMemsetAsync(c->init_logits, 0, bytes, st), "memset");
+  if (s == CPRA_OK) {
+    copy_rows_launch(c->N, c->S, tmp, c->init_logits, c->S_pad, c->act_dt, st);
+    c->launches += 1;
+    s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+  }
+  cudaFree(tmp);
+  return s;
 }
 
 // ------------------------------------------------------------ op level

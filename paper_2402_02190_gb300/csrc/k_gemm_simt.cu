@@ -130,7 +130,14 @@ gemm_simt_kernel(GemmArgs g) {
           v += g.bias[n];
           st_el(g.out0, g.d0, m * g.ld0 + n, v > 0.f ? v : 0.f);
           break;
+        case EPI_BIAS:
+          st_el(g.out0, g.d0, m * g.ld0 + n, n < nval ? v + g.bias[n] : 0.f);
+          break;
         case EPI_BIAS_SIGMOID:
+          if (g.addend && n < nval)
+            v += g.d_add == DT_BF16
+                     ? __bfloat162float(static_cast<const bf16*>(g.addend)[m * g.ld_add + n])
+                     : static_cast<const float*>(g.addend)[m * g.ld_add + n];
           v = (n < nval) ? 1.0f / (1.0f + expf(-(v + g.bias[n]))) : 0.f;
           st_el(g.out0, g.d0, m * g.ld0 + n, v);
           break;

@@ -150,6 +150,9 @@ struct TcParams {
   const float* row_scale = nullptr;
   int n_valid = 0;
   int* err_flag = nullptr;
+  const void* addend = nullptr;
+  int64_t ld_add = 0;
+  int d_add = DT_BF16;
 };
 
 // Output staging: each epilogue warp owns two buffers of 32 rows x 16
@@ -213,6 +216,20 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
       return 0;
     }
     case EPI_BIAS_SIGMOID: {
+      if (p.addend && row < p.M) {  // per-element offset of the pre-activation
+        float a[16];
+        if (p.d_add == DT_BF16) {
+          const bf16* src = static_cast<const bf16*>(p.addend) + row * p.ld_add + n;
+          load16(src, a);
+          load16(src + 8, a + 8);
+        } else {
+          const float* src = static_cast<const float*>(p.addend) + row * p.ld_add + n;
+#pragma unroll
+          for (int q = 0; q < 16; q += 4) load16(src + q, a + q);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += a[k];
+      }
       const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -222,6 +239,20 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
         for (int e = 0; e < 4; ++e) {
           const int k = 4 * j + e;
           v[k] = (n + k < p.n_valid) ? __fdividef(1.0f, 1.0f + __expf(-(v[k] + bb[e]))) : 0.f;
+        }
+      }
+      return 0;
+    }
+    case EPI_BIAS: {
+      const float4* b4 = reinterpret_cast<const float4*>(p.bias + n);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 b = __ldg(b4 + j);
+        const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * j + e;
+          v[k] = (n + k < p.n_valid) ? v[k] + bb[e] : 0.f;
         }
       }
       return 0;
@@ -698,6 +729,8 @@ void init_driver() {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
       cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_RELU_BITS>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_gemm_nt_kernel<EPI_BIAS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) != cudaSuccess ||
       cudaFuncSetAttribute(tc_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            g_max_smem) != cudaSuccess) {
     cudaGetLastError();
@@ -759,7 +792,7 @@ bool tc_gemm_supported(const GemmArgs& g) {
   if (!g_ok) return false;
   if (g.da != DT_BF16 || g.db != DT_BF16 || !g.a_kmajor || !g.b_kmajor) return false;
   if (g.epi != EPI_BIAS_RELU && g.epi != EPI_BIAS_SIGMOID && g.epi != EPI_SPLIT &&
-      g.epi != EPI_RELU_BITS)
+      g.epi != EPI_RELU_BITS && g.epi != EPI_BIAS)
     return false;
   if (g.K < kBK || g.K % 8 || g.lda % 8 || g.ldb % 8) return false;
   if (g.Nc % 16 || pick_bn(g.Nc) == 0) return false;
@@ -805,6 +838,9 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.d1 = g.d1;
   p.split = g.split;
   p.row_scale = g.row_scale;
+  p.addend = g.addend;
+  p.ld_add = g.ld_add;
+  p.d_add = g.d_add;
   p.n_valid = g.n_valid > 0 ? g.n_valid : g.Nc;
   p.err_flag = g.err_flag;
   CUtensorMap ta, tb, to0, to1;
@@ -836,6 +872,9 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
       break;
     case EPI_RELU_BITS:
       tc_gemm_nt_kernel<EPI_RELU_BITS><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+    case EPI_BIAS:
+      tc_gemm_nt_kernel<EPI_BIAS><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
       break;
     default:
       tc_gemm_nt_kernel<EPI_SPLIT><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);

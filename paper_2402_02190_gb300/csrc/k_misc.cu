@@ -56,18 +56,6 @@ __global__ void weight_shadows_kernel(const float* __restrict__ th, int H0, int 
   }
 }
 
-// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
-__device__ __forceinline__ float u24(uint64_t seed, uint64_t tag, uint64_t idx) {
-  const uint64_t h = splitmix64(seed ^ splitmix64(tag) ^ (idx * 0xD1B54A32D192ED03ull));
-  return (float)(h >> 40) * (1.0f / 16777216.0f);  // [0, 1)
-}
-
 __global__ void init_uniform_kernel(float* p, int64_t n, float bound, uint64_t seed,
                                     uint64_t tag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -79,9 +67,7 @@ __global__ void init_uniform_kernel(float* p, int64_t n, float bound, uint64_t s
 __global__ void init_normal_kernel(float* p, int64_t n, uint64_t seed, uint64_t tag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float u1 = u24(seed, tag, 2 * (uint64_t)i) + (0.5f / 16777216.0f);
-    const float u2 = u24(seed, tag, 2 * (uint64_t)i + 1);
-    p[i] = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+    p[i] = normal_at(seed, tag, (uint64_t)i);
   }
 }
 

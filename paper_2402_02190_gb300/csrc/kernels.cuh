@@ -108,13 +108,15 @@ void eval_finalize(const unsigned long long* counters, int S, int problem,
 
 // ---------------------------------------------------------------- GEMM
 enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3,
-           EPI_RELU_BITS = 4 };
+           EPI_RELU_BITS = 4, EPI_BIAS = 5 };
 // C[m, n] = sum_k A(m, k) B(n, k), FP32 accumulation.
 //   A(m, k) = A[m*lda + k] if a_kmajor else A[k*lda + m]; same for B.
 // Epilogues:
 //   EPI_PARTIAL      out0 (f32) + z*M*ld0 <- C for split z of gridDim.z
 //   EPI_BIAS_RELU    out0[m, n] <- max(C + bias[n], 0)
-//   EPI_BIAS_SIGMOID out0[m, n] <- 1/(1+exp(-(C + bias[n]))) for n < n_valid, else 0
+//   EPI_BIAS         out0[m, n] <- C + bias[n] for n < n_valid, else 0
+//   EPI_BIAS_SIGMOID out0[m, n] <- 1/(1+exp(-(C + bias[n] [+ addend[m*ld_add + n]])))
+//                    for n < n_valid, else 0 (addend, dtype d_add, may be null)
 //   EPI_SPLIT        n < split: out0[m, n] <- C; else out1[m, n-split] <- C * row_scale[m]
 //   EPI_RELU_BITS    ReLU mask only: bit (n % 16) of the uint16 out0[m*ld0 + n/16] is
 //                    1[h > 0] for h = max(C + bias[n], 0) rounded to dtype d0 (so the
@@ -144,6 +146,9 @@ struct GemmArgs {
   int n_valid = 0;
   int splits = 1;
   int* err_flag = nullptr;  // device word; bit 1 set if a bounded wait gave up
+  const void* addend = nullptr;  // EPI_BIAS_SIGMOID: per-element pre-activation offset
+  int64_t ld_add = 0;
+  int d_add = DT_F32;
 };
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
 // out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.
@@ -176,6 +181,25 @@ struct EarlyStopState {
 void early_stop_launch(const float* terms, const float* lambda, int S, float gamma, float tol,
                        int patience, long long t, long long updates, EarlyStopState* st,
                        cudaStream_t stream);
+// ---------------------------------------------------------------- warm start (k_warm.cu)
+// Node features [N x F]: 1, deg/8, then N(0,1) from the stream of `seed`.
+void ws_features_launch(int64_t N, const int* rowptr, uint64_t seed, int F, float* out,
+                        cudaStream_t st);
+void inv_degree_launch(int64_t N, const int* rowptr, float* inv, cudaStream_t st);
+// Binary cross-entropy of logits Z [N x ldz] against target bits [N x ceil(S/32)]:
+// G = (sigmoid(Z) - y) * inv_count (dtype dg, pad columns up to S_pad zeroed);
+// per-block loss sums to partial[grid]; returns the grid.
+int ws_bce_launch(int64_t N, int S, int S_pad, const float* Z, int64_t ldz, const uint32_t* bits,
+                  void* G, int64_t ldg, int dg, float inv_count, float* partial, int max_grid,
+                  cudaStream_t st);
+// Per-block column sums of X [N x C] (dtype dx) over contiguous row ranges
+// into partial[blocks][C]; returns the number of blocks (<= max_blocks).
+int rows_colsum_launch(int64_t N, int C, const void* X, int64_t ldx, int dx, float* partial,
+                       int max_blocks, cudaStream_t st);
+// BF16 copies Ws [rows_pad x cols] and Wt [cols x rows_pad] of FP32 W [rows x cols].
+void weight_pair_launch(const float* W, int rows, int cols, int rows_pad, void* Ws, void* Wt,
+                        cudaStream_t st);
+
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd,
                       int ddst, cudaStream_t st);
 // BF16 shadows of the dense weights:

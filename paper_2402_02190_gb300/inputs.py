@@ -217,3 +217,52 @@ def seeded_P(N: int, S: int, seed: int, special: bool = True) -> np.ndarray:
         P[1, :] = np.float32(0.25)          # constant row: VAR == 0
         P[3, :] = np.float32(0.5)           # constant row at the threshold
     return P
+
+
+# ------------------------------------------------------------ warm start
+def ws_param_count(F: int, H: int, S: int) -> int:
+    """Flat size of the warm-start network: three Eq. GCN layers F -> H -> H -> S."""
+    return 2 * H * F + H + 2 * H * H + H + 2 * S * H + S
+
+
+def seeded_ws_params(F: int, H: int, S: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """U(+-scale/sqrt(fan_in)) per block, float32, in the flat layout."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for fan, n in ((2 * F, 2 * H * F), (2 * F, H), (2 * H, 2 * H * H), (2 * H, H),
+                   (2 * H, 2 * S * H), (2 * H, S)):
+        b = scale / np.sqrt(fan)
+        out.append(rng.uniform(-b, b, size=n))
+    return np.concatenate(out).astype(np.float32)
+
+
+def seeded_ws_features(rowptr, F: int, seed: int) -> np.ndarray:
+    """Host stand-in for the network's node features: 1, deg/8, then N(0,1)."""
+    rowptr = np.asarray(rowptr)
+    N = len(rowptr) - 1
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(N, F))
+    X[:, 0] = 1.0
+    X[:, 1] = np.diff(rowptr) / 8.0
+    return X.astype(np.float32)
+
+
+def seeded_bits(N: int, S: int, seed: int, p: float = 0.3) -> np.ndarray:
+    """Random 0/1 targets [N, S] packed as uint32 [N, ceil(S/32)] (bit s % 32 of word s // 32)."""
+    rng = np.random.default_rng(seed)
+    Y = (rng.random((N, S)) < p).astype(np.uint8)
+    W = (S + 31) // 32
+    out = np.zeros((N, W), dtype=np.uint32)
+    for s in range(S):
+        out[:, s // 32] |= (Y[:, s].astype(np.uint32) << np.uint32(s % 32))
+    return out
+
+
+def unpack_bits(bits, S: int) -> np.ndarray:
+    """uint32 [N, ceil(S/32)] -> 0/1 uint8 [N, S]."""
+    bits = np.asarray(bits, dtype=np.uint32)
+    N = bits.shape[0]
+    out = np.zeros((N, S), dtype=np.uint8)
+    for s in range(S):
+        out[:, s] = (bits[:, s // 32] >> np.uint32(s % 32)) & np.uint32(1)
+    return out

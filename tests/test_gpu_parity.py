@@ -198,7 +198,7 @@ STEP_CASES = [
 ]
 
 
-def _run_step_case(case, precision, keep_emb_grad=1, recompute=0):
+def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None):
     problem, div, alpha, nu, S, H, N, gk = case
     rp, col = graph_of(gk, N, seed=N + S)
     g = O.Graph(rp, col)
@@ -216,6 +216,8 @@ def _run_step_case(case, precision, keep_emb_grad=1, recompute=0):
                        (cpra.T_THETA_V, vt), (cpra.T_EMB_M, mx), (cpra.T_EMB_V, vx),
                        (cpra.T_STEP, np.array([t_prev]))):
         solver.set(which, arr)
+    if init_logits is not None:
+        solver.set_init_logits(init_logits)
     terms = solver.step(t_idx, want_terms=True).astype(np.float64)
     out = dict(P=solver.P(), grad=solver.get(cpra.T_GRAD), gX0=solver.get(cpra.T_EMB_GRAD),
                theta=solver.get(cpra.T_THETA), X0=solver.get(cpra.T_EMB), terms=terms,
@@ -228,6 +230,10 @@ def _run_step_case(case, precision, keep_emb_grad=1, recompute=0):
     if precision == cpra.BF16:
         # the ReLU sign is decided at the kernels' (bfloat16 operand) precision
         cfg["relu_decision"] = "bf16"
+    if init_logits is not None:
+        # the library keeps the offset in the dense layers' dtype
+        cfg["init_logits"] = (O.bf16_round(init_logits) if precision == cpra.BF16
+                              else np.asarray(init_logits, dtype=np.float64))
     ref = O.step(g, theta, X0, cfg, t=t_prev + 1,
                  adam_state=dict(m_theta=mt, v_theta=vt, m_X0=mx.reshape(N, H),
                                  v_X0=vx.reshape(N, H)))
@@ -297,6 +303,37 @@ def test_fused_embedding_update_without_stored_gradient(precision):
     tol = 1e-5 if precision == cpra.FP32 else 2e-2
     dref = ref["X0_next"] - X0
     assert np.linalg.norm(fused["X0"].reshape(X0.shape) - ref["X0_next"]) <= 10 * tol * np.linalg.norm(dref)
+
+
+@pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])
+@pytest.mark.parametrize("ci", [0, 2])
+def test_full_step_with_init_logits_matches_oracle(precision, ci):
+    """Warm-start offset L0 on the head's pre-activation (cpra_set_init_logits)
+    through a full step, against the oracle forward with the same offset."""
+    case = STEP_CASES[ci]
+    S, N = case[4], case[6]
+    L0 = np.random.default_rng(11).normal(size=(N, S)).astype(np.float32) * 2.0
+    tol = 1e-5 if precision == cpra.FP32 else 2e-2
+    out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, precision, init_logits=L0)
+    _check_step(out, ref, g, lam, gamma, theta, X0, S, case[5], tol, case[0])
+
+
+def test_init_logits_cleared_restores_plain_network():
+    rp, col = I.random_regular_graph(200, 3, seed=5)
+    lam = I.lambda_linspace(1, 4, 8)
+    a = cpra.Solver(rp, col, lam=lam, problem=cpra.MIS, S=8, seed=2)
+    b = cpra.Solver(rp, col, lam=lam, problem=cpra.MIS, S=8, seed=2)
+    b.set_init_logits(np.full((200, 8), 3.0, np.float32))
+    b.set_init_logits(None)
+    for t in range(3):
+        a.step(t)
+        b.step(t)
+    assert np.array_equal(a.P(), b.P())
+    # ld < S is rejected
+    st = cpra.lib().cpra_set_init_logits(a.ctx, cpra._ptr(np.zeros(8, np.float32)), 4, 0)
+    assert st == cpra.CPRA_EINVAL
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])

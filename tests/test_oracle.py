@@ -198,6 +198,30 @@ def test_forward_reduces_to_mlp_without_neighbour_weights():
             assert out[v, s] == pytest.approx(1.0 / (1.0 + np.exp(-z)), rel=1e-13)
 
 
+def test_init_logits_offset_of_the_head():
+    """The warm-start offset L0 enters the head's pre-activation: with every
+    weight and bias zero P = sigmoid(L0) exactly, and an offset that is
+    constant per shot is the same as adding it to b2."""
+    rp, col = I.random_regular_graph(30, 3, seed=2)
+    g = O.Graph(rp, col)
+    N, H, S = 30, 16, 5
+    rng = np.random.default_rng(0)
+    L0 = rng.normal(size=(N, S)) * 3
+    theta0 = np.zeros(O.param_count(H, H, S))
+    X0 = rng.normal(size=(N, H))
+    P = O.forward(g, theta0, X0, H, H, S, init_logits=L0)["P"]
+    assert np.array_equal(P, 1.0 / (1.0 + np.exp(-L0)))
+    theta, X0 = I.seeded_params(N, H, H, S, seed=4)
+    c = rng.normal(size=S)
+    lay = I.param_layout(H, H, S)
+    off, shape = lay["b2"]
+    theta_b = theta.astype(np.float64).copy()
+    theta_b[off:off + S] += c
+    Pa = O.forward(g, theta, X0, H, H, S, init_logits=np.tile(c, (N, 1)))["P"]
+    Pb = O.forward(g, theta_b, X0, H, H, S)["P"]
+    assert np.allclose(Pa, Pb, rtol=0, atol=1e-15)
+
+
 def test_forward_on_complete_graph_closed_form():
     """On K_n the neighbour mean is (sum of all rows - own row) / (n - 1)."""
     n = 6
