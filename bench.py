@@ -379,6 +379,100 @@ def run_reference(args):
     }))
 
 
+# ------------------------------------------------------------ quality mode
+def run_quality(args):
+    """The metric's second half: wall time for the BF16 + warm-start form to
+    come within 1% of the best MIS the plain FP32 form finds on the same graph
+    (the workload's graph, shots and widths), plus the warm-start network's
+    training summary and a held-out comparison (objective gap, steps saved)."""
+    import torch
+    from paper_2402_02190_gb300 import cpra
+    from paper_2402_02190_gb300 import warm as WM
+    w = WORKLOADS[args.workload]
+    S, H, lam_spec = w["S"], w["H"], w["lam"]
+    lam = make_lambda(w)
+    q = args.q_steps
+    out = {"metric": "wall time to within 1% of the FP32 form's best MIS (BF16 + warm start)",
+           "unit": "s", "higher_is_better": False, "mode": "quality", "data": "synthetic",
+           "config": {"workload": args.workload, "steps": q, "eval_every": args.q_eval,
+                      "warm_graphs": args.q_train, "warm_heldout": args.q_heldout}}
+    # 1. targets from plain CPRA on seeded training graphs (BF16)
+    t0 = time.perf_counter()
+    graphs = WM.training_graphs(args.q_train + args.q_heldout, seed=77, n_min=1000, n_max=5000)
+    train, held = graphs[:args.q_train], graphs[args.q_train:]
+    dataset = []
+    for k, (rp, col, d) in enumerate(train):
+        bits, _ = WM.cpra_targets(rp, col, S, lam, args.q_target_steps, cpra.BF16, H=64, seed=k + 1)
+        dataset.append((rp, col, bits, 1000 + k))
+    t_targets = time.perf_counter() - t0
+    # 2. fit the warm-start network
+    max_n = max(len(g[0]) - 1 for g in train) * args.q_batch
+    max_e = max(int(g[0][-1]) for g in train) * args.q_batch
+    net = cpra.WarmStartNet(max_n, max_e, F=16, H=64, S=S, precision=cpra.BF16, lr=3e-3)
+    t0 = time.perf_counter()
+    losses = WM.train_network(net, dataset, args.q_epochs, args.q_batch)
+    t_fit = time.perf_counter() - t0
+    theta = net.params(0)
+    out["warm_training"] = {"graphs": len(dataset), "target_steps": args.q_target_steps,
+                            "target_seconds": t_targets, "fit_seconds": t_fit,
+                            "epochs": args.q_epochs, "loss_first": losses[0], "loss_last": losses[-1]}
+    # 3. held-out graphs: plain BF16 from random init vs BF16 + warm start
+    gaps, saved, reached = [], [], 0
+    for k, (rp, col, d) in enumerate(held):
+        big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
+        big.set_params(theta)
+        L0 = WM.predict_logits(big, rp, col, 5000 + k)
+        plain = WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16, H=64, seed=7)
+        warm = WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16, H=64, seed=7,
+                            init_logits=L0, gamma0=args.q_warm_gamma0)
+        big.close()
+        best = plain[-1][2]
+        gaps.append((warm[-1][2] - best) / max(best, 1))
+        tp = WM.time_to_reach(plain, 0.99 * best)
+        tw = WM.time_to_reach(warm, 0.99 * best)
+        if tw is not None:
+            reached += 1
+            saved.append(tp[1] - tw[1])
+    out["heldout"] = {"graphs": len(held), "mean_relative_gap_final": float(np.mean(gaps)),
+                      "reached_99pct": reached,
+                      "mean_steps_saved_to_99pct": float(np.mean(saved)) if saved else None}
+    # 4. the workload graph: FP32 plain vs BF16 + warm start, wall clock
+    rp, col = make_graph(w)
+    fp32 = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.FP32, H=H, seed=1)
+    best = fp32[-1][2]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
+    big.set_params(theta)
+    L0 = WM.predict_logits(big, rp, col, 99)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    warm = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1, init_logits=L0,
+                        gamma0=args.q_warm_gamma0, t0=t0)
+    big.close()
+    plain16 = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1)
+    # the warm start under the full annealing schedule (gamma from -2)
+    warm_full = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1, init_logits=L0,
+                             gamma0=-2.0)
+    target = 0.99 * best
+    r32, rw, r16, rwf = (WM.time_to_reach(x, target) for x in (fp32, warm, plain16, warm_full))
+    out["traces"] = {k: [(round(a, 4), b, c) for a, b, c in x[::max(1, len(x) // 10)]]
+                     for k, x in (("fp32", fp32), ("bf16_warm", warm), ("bf16_plain", plain16))}
+    out["fp32"] = {"best": best, "seconds_to_99pct": r32[0] if r32 else None,
+                   "steps_to_99pct": r32[1] if r32 else None, "total_seconds": fp32[-1][0]}
+    out["bf16_warm"] = {"best": warm[-1][2], "seconds_to_99pct": rw[0] if rw else None,
+                        "steps_to_99pct": rw[1] if rw else None, "total_seconds": warm[-1][0],
+                        "warm_inference_seconds": t_inf}
+    out["bf16_plain"] = {"best": plain16[-1][2], "seconds_to_99pct": r16[0] if r16 else None,
+                         "steps_to_99pct": r16[1] if r16 else None, "total_seconds": plain16[-1][0]}
+    out["bf16_warm_full_schedule"] = {"best": warm_full[-1][2],
+                                      "seconds_to_99pct": rwf[0] if rwf else None,
+                                      "steps_to_99pct": rwf[1] if rwf else None}
+    out["value"] = rw[0] if rw else None
+    out["vs_fp32_seconds"] = r32[0] if r32 else None
+    print(json.dumps(out))
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--cpu-baseline-child":
         cpu_baseline_child(sys.argv[2:])
@@ -392,8 +486,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--recompute", type=int, choices=[0, 1], default=None,
                     help="override the workload's activation-recompute setting")
+    ap.add_argument("--quality", action="store_true",
+                    help="time-to-quality run: FP32 plain vs BF16 + warm start on the workload graph")
+    ap.add_argument("--q-steps", type=int, default=2000)
+    ap.add_argument("--q-eval", type=int, default=50)
+    ap.add_argument("--q-train", type=int, default=96)
+    ap.add_argument("--q-heldout", type=int, default=8)
+    ap.add_argument("--q-target-steps", type=int, default=1000)
+    ap.add_argument("--q-epochs", type=int, default=40)
+    ap.add_argument("--q-batch", type=int, default=8)
+    ap.add_argument("--q-warm-gamma0", type=float, default=-0.5)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
+    if args.quality:
+        run_quality(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
