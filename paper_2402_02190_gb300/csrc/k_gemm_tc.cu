@@ -771,10 +771,18 @@ bool make_out_map(CUtensorMap* m, const void* base, int dt, int64_t cols, int64_
   return r == CUDA_SUCCESS;
 }
 
-int pick_bn(int Nc) {
-  if (Nc <= 256) return Nc;
-  for (int bn = 256; bn >= 16; bn -= 16)
-    if (Nc % bn == 0) return bn;
+// Shared memory a CTA needs with BN output columns (weights resident) and
+// the minimum of two A stages.
+size_t tc_smem_need(int bn, int64_t K) {
+  const int n_kb = static_cast<int>((K + kBK - 1) / kBK);
+  return 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal + 2 * kStageBytes + 256;
+}
+
+// Widest n tile (a multiple of 16 dividing Nc, at most 256) whose weight
+// slice stays resident in shared memory; 0 if none does.
+int pick_bn(int Nc, int64_t K) {
+  for (int bn = Nc < 256 ? Nc : 256; bn >= 16; bn -= 16)
+    if (Nc % bn == 0 && tc_smem_need(bn, K) <= static_cast<size_t>(g_max_smem)) return bn;
   return 0;
 }
 
@@ -795,14 +803,10 @@ bool tc_gemm_supported(const GemmArgs& g) {
       g.epi != EPI_RELU_BITS && g.epi != EPI_BIAS)
     return false;
   if (g.K < kBK || g.K % 8 || g.lda % 8 || g.ldb % 8) return false;
-  if (g.Nc % 16 || pick_bn(g.Nc) == 0) return false;
+  if (g.Nc % 16 || pick_bn(g.Nc, g.K) == 0) return false;
   if (g.epi == EPI_SPLIT && g.split % 16) return false;
   if ((g.epi != EPI_RELU_BITS && g.ld0 % 8) || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
-  const int bn = pick_bn(g.Nc);
-  const int n_kb = static_cast<int>((g.K + kBK - 1) / kBK);
-  const size_t need =
-      1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal + 2 * kStageBytes + 256;
-  return need <= static_cast<size_t>(g_max_smem);
+  return true;
 }
 
 int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
@@ -810,7 +814,7 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.M = g.M;
   p.Nc = g.Nc;
   p.K = static_cast<int>(g.K);
-  p.BN = pick_bn(g.Nc);
+  p.BN = pick_bn(g.Nc, g.K);
   p.n_tiles_n = g.Nc / p.BN;
   p.n_kb = (p.K + kBK - 1) / kBK;
   p.m_tiles = (g.M + kBM - 1) / kBM;

@@ -195,6 +195,9 @@ STEP_CASES = [
     (O.MIS, O.DIV_STD, 4, 0.3, 24, 32, 700, ("er", 5)),
     (O.MAXCUT, O.DIV_VAR, 2, 0.1, 64, 32, 1200, ("er", 10)),
     (O.MAXCUT, O.DIV_STD, 2, 0.2, 100, 48, 517, ("rrg", 20)),
+    # H = 256: the layer-1 weights (256 x 512 BF16) exceed shared memory as one
+    # tile, so the tensor-core GEMM splits the output columns into two tiles
+    (O.MIS, O.DIV_STD, 2, 0.0, 100, 256, 600, ("rrg", 20)),
 ]
 
 
