@@ -265,8 +265,11 @@ def run_gpu(args):
 
     solver = cpra.Solver(rp, col, lam=lam, **kw)
     stream = solver.stream          # the stream every library kernel is launched on
-    for t in range(args.warmup):
-        solver.step(t)
+    if args.graph:
+        solver.steps(0, args.warmup)   # captures the step graph before timing
+    else:
+        for t in range(args.warmup):
+            solver.step(t)
     torch.cuda.synchronize()
     cpra.cpra_profile_enable(solver.ctx, True)
     cpra.cpra_profile_read(solver.ctx)          # reset counters
@@ -277,8 +280,11 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
-        for t in range(args.warmup, args.warmup + args.steps):
-            solver.step(t)
+        if args.graph:    # one call: a captured step replayed (cpra_steps)
+            solver.steps(args.warmup, args.steps)
+        else:
+            for t in range(args.warmup, args.warmup + args.steps):
+                solver.step(t)
         e1.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -287,6 +293,21 @@ def run_gpu(args):
     prof = cpra.cpra_profile_read(solver.ctx)
     launches = solver.launches - launches0
     ms = max_over_ranks(ms, dist)
+    graph_ms = None
+    if not args.graph:
+        # the same steps once more through cpra_steps (one captured step
+        # replayed as a CUDA graph), timed the same way, as a second figure
+        cpra.cpra_profile_enable(solver.ctx, False)
+        t_next = args.warmup + args.steps
+        solver.steps(t_next, args.warmup)            # capture + warm replays
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        solver.steps(t_next + args.warmup, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = max_over_ranks(e0.elapsed_time(e1), dist)
     solver.close()
     del solver
     torch.cuda.synchronize()
@@ -329,6 +350,7 @@ def run_gpu(args):
                    "problem": ["MIS", "MaxCut"][w["problem"]], "nu": w["nu"],
                    "precision": ["fp32", "bf16"][w["precision"]], "parallelism": f"replicas{world}",
                    "recompute": recompute,
+                   "launch": "one captured step replayed (CUDA graph)" if args.graph else "per-step launches",
                    "l2": f"inputs larger than L2 (P = {N * S * 4 / 1e9:.2f} GB), no flush"},
         "roofline": {"kernel": "loss_fused", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -339,6 +361,10 @@ def run_gpu(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "seconds": e2e_s},
         "gpu_launches": launches,
+        "graph": None if graph_ms is None else {
+            "ms_per_step": graph_ms / args.steps,
+            "value": replica_throughput(world, nnz * S * args.steps, graph_ms / 1e3),
+            "how": "the same steps through cpra_steps: one captured step replayed as a CUDA graph"},
         "clocks": clk.summary(),
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / args.steps)
                                 for k, v in prof.items() if v[1]},
@@ -486,6 +512,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--recompute", type=int, choices=[0, 1], default=None,
                     help="override the workload's activation-recompute setting")
+    ap.add_argument("--graph", action="store_true",
+                    help="time the steps through cpra_steps (one captured step replayed as a CUDA "
+                         "graph); per-kernel times are then not available")
     ap.add_argument("--quality", action="store_true",
                     help="time-to-quality run: FP32 plain vs BF16 + warm start on the workload graph")
     ap.add_argument("--q-steps", type=int, default=2000)

@@ -168,6 +168,13 @@ CPRA_API cpra_status cpra_forward(cpra_ctx* ctx, const float* theta_dev, const f
 CPRA_API cpra_status cpra_backward(cpra_ctx* ctx, float scale, float* grad_theta_dev,
                                    float* grad_emb_dev);
 
+/* n consecutive steps with schedule indices t0 .. t0+n-1, the same as n
+   cpra_step calls without loss readback: the first runs directly, the rest
+   replay one step captured as a CUDA graph (captured on the first call that
+   needs it, with the context stream; per-step values such as gamma_t and
+   the Adam bias corrections are computed on the device).  Asynchronous. */
+CPRA_API cpra_status cpra_steps(cpra_ctx* ctx, int64_t t0, int64_t n);
+
 /* Copies the evaluation of the most recent cpra_step (or, before any step,
    of a fresh forward pass) to the host.  out: host [S]; pair_hamming_sum:
    host int64 receiving sum_i k_i (S - k_i) = sum_{s<l} d_H(x_s, x_l)

@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
     "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
-    "cpra_set_init_logits", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
+    "cpra_set_init_logits", "cpra_steps", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
     "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
     "cpra_ws_set_params", "cpra_ws_destroy",
 )
@@ -107,6 +107,7 @@ def lib():
         "cpra_param_count": (i64, [vp]),
         "cpra_launch_count": (i64, [vp]),
         "cpra_early_stop_step": (i64, [vp]),
+        "cpra_steps": (i32, [vp, i64, i64]),
         "cpra_set_init_logits": (i32, [vp, vp, i64, i32]),
         "cpra_profile_enable": (None, [vp, C.c_int]),
         "cpra_profile_read": (i32, [vp, vp, vp, i32]),
@@ -305,6 +306,10 @@ def cpra_launch_count(ctx) -> int:
     return int(lib().cpra_launch_count(ctx))
 
 
+def cpra_steps(ctx, t0: int, n: int) -> None:
+    _check(lib().cpra_steps(ctx, int(t0), int(n)), ctx)
+
+
 def cpra_early_stop_step(ctx) -> int:
     return int(lib().cpra_early_stop_step(ctx))
 
@@ -427,6 +432,9 @@ class Solver:
 
     def solve(self, steps: int, eval_every: int):
         return cpra_solve(self.ctx, steps, eval_every)
+
+    def steps(self, t0: int, n: int) -> None:
+        cpra_steps(self.ctx, t0, n)
 
     def early_stop_step(self) -> int:
         return cpra_early_stop_step(self.ctx)

@@ -120,6 +120,12 @@ struct cpra_ctx {
   uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
   EarlyStopState* es = nullptr;   // early-stopping monitor (device)
   void* init_logits = nullptr;    // warm start: N x S_pad act dtype, own cudaMalloc
+  StepScalars* sc = nullptr;      // per-step gamma / bias corrections (device)
+  // one captured training step, replayed by cpra_steps / cpra_solve
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_launches = 0;     // kernels per replay
+  bool capturing = false;
   bool recompute = false;
   uint32_t* xbits = nullptr;
   float* loss_part = nullptr;
@@ -274,6 +280,7 @@ size_t carve(cpra_ctx* c, void* base) {
   c->wg_part = cv.take<float>(c->wg_part_floats);
   c->err_flag = cv.take<int>(4);
   c->es = cv.take<EarlyStopState>(1);
+  c->sc = cv.take<StepScalars>(1);
   c->W1s = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W1t = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W2s = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
@@ -300,7 +307,7 @@ struct Region {
   int id;
   size_t slot = (size_t)-1;
   Region(cpra_ctx* ctx, int kid) : c(ctx), id(kid) {
-    if (!c->prof) return;
+    if (!c->prof || c->capturing) return;
     if (c->prof_used == c->prof_ring.size()) {
       // flush: synchronise and accumulate
       cudaStreamSynchronize(c->stream);
@@ -414,7 +421,8 @@ void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_
   c->launches += 2;
 }
 
-cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
+cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
+                                 const StepScalars* sc = nullptr) {
   const int64_t N = c->N;
   const int H0 = c->H0, H1 = c->H1;
   const int max_grid = c->num_sms * 8;
@@ -469,7 +477,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss) {
     a.N = N; a.S = c->S; a.ldp = c->S_pad; a.ldg = c->S_pad;
     a.rowptr = c->rowptr; a.col = c->col; a.P = c->P; a.lambda = c->lambda_d;
     a.problem = c->cfg.problem; a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
-    a.grad_kind = 0; a.gamma = gamma; a.nu = c->cfg.nu;
+    a.grad_kind = 0; a.gamma = gamma; a.sc = do_loss ? sc : nullptr; a.nu = c->cfg.nu;
     a.G = c->GZ2; a.dg = c->act_dt; a.xbits = c->xbits;
     a.partials = c->loss_part; a.pstride = c->pstride; a.err_flag = c->err_flag;
     a.do_loss = do_loss ? 1 : 0;
@@ -588,6 +596,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       if (fuse_adam) {
         a.adam = 1;
         a.halt = halt_flag(c);
+        a.sc = c->sc;
         if (!c->cfg.keep_emb_grad) a.Y = nullptr;
         a.emb = c->X0m; a.emb_m = c->X0_m; a.emb_v = c->X0_v;
         a.shadow = c->XM; a.lds = 2 * H0;
@@ -614,11 +623,11 @@ cpra_status run_update(cpra_ctx* c) {
   {
     Region r(c, K_ADAM);
     adam_launch(c->nparam, c->theta, c->theta_m, c->theta_v, c->grad, c->cfg.lr, c->cfg.beta1,
-                c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, halt_flag(c), c->stream);
+                c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, halt_flag(c), c->sc,
+                c->stream);
     c->launches += 1;
     refresh_shadows(c);
   }
-  c->opt_steps += 1;
   return CPRA_OK;
 }
 
@@ -798,23 +807,78 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   return CPRA_OK;
 }
 
-cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
-  if (!c) return CPRA_EINVAL;
-  c->fwd_valid = false;
-  const float gamma = gamma_at(c->cfg, t);
-  cpra_status s = run_forward_and_loss(c, gamma, true);
+namespace {
+
+// The kernels of one training step after its scalars are in c->sc:
+// forward + loss, early-stopping monitor, adjoint with the fused embedding
+// update, parameter Adam.  Launches only (no host synchronisation), so the
+// sequence can be captured into a CUDA graph.
+cpra_status launch_step_body(cpra_ctx* c) {
+  cpra_status s = run_forward_and_loss(c, 0.f, true, c->sc);
   if (s != CPRA_OK) return s;
   if (c->cfg.es_patience > 0) {
-    early_stop_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S, gamma,
-                      c->cfg.es_tol, c->cfg.es_patience, (long long)t, (long long)c->opt_steps,
-                      c->es, c->stream);
+    early_stop_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S,
+                      c->cfg.es_tol, c->cfg.es_patience, c->sc, c->es, c->stream);
     c->launches += 1;
   }
   const bool emb = c->cfg.train_embedding != 0;
   s = run_backward(c, emb, /*fuse_adam=*/emb);
   if (s != CPRA_OK) return s;
-  s = run_update(c);
+  return run_update(c);
+}
+
+void launch_step_scalars(cpra_ctx* c, bool from_device, int64_t t) {
+  step_scalars_launch(c->sc, from_device ? 1 : 0, (long long)t, (long long)c->opt_steps,
+                      c->cfg.gamma0, c->cfg.gamma1, (long long)c->cfg.schedule_steps,
+                      c->cfg.beta1, c->cfg.beta2, c->stream);
+  c->launches += 1;
+}
+
+void drop_graph(cpra_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+// Captures one step (scalars read from the device counters + body) on the
+// context stream.
+cpra_status capture_step(cpra_ctx* c) {
+  drop_graph(c);
+  const int64_t before = c->launches;
+  c->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  cpra_status s = CPRA_OK;
+  if (e == cudaSuccess) {
+    launch_step_scalars(c, true, 0);
+    s = launch_step_body(c);
+    e = cudaStreamEndCapture(c->stream, &c->graph);
+  }
+  c->capturing = false;
+  c->graph_launches = c->launches - before;
+  c->launches = before;
+  if (s != CPRA_OK) {
+    drop_graph(c);
+    return s;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+  if (e != cudaSuccess) {
+    drop_graph(c);
+    return cuda_check(c, e, "step graph capture");
+  }
+  return CPRA_OK;
+}
+
+}  // namespace
+
+cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
+  if (!c) return CPRA_EINVAL;
+  c->fwd_valid = false;
+  launch_step_scalars(c, false, t);
+  cpra_status s = launch_step_body(c);
   if (s != CPRA_OK) return s;
+  c->opt_steps += 1;
+  c->have_eval = true;
   s = cuda_check(c, cudaGetLastError(), "step kernels");
   if (s != CPRA_OK) return s;
   if (loss_terms_out) {
@@ -827,6 +891,27 @@ cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
   return CPRA_OK;
 }
 
+cpra_status cpra_steps(cpra_ctx* c, int64_t t0, int64_t n) {
+  if (!c || n < 0) return c ? fail(c, CPRA_EINVAL, "cpra_steps: n < 0") : CPRA_EINVAL;
+  if (n == 0) return CPRA_OK;
+  // the first step runs directly: it sets the device counters to (t0 + 1,
+  // updates + 1) that the replays advance from
+  cpra_status s = cpra_step(c, t0, nullptr);
+  if (s != CPRA_OK || n == 1) return s;
+  if (!c->gexec) {
+    s = capture_step(c);
+    if (s != CPRA_OK) return s;
+  }
+  for (int64_t k = 1; k < n; ++k) {
+    cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "step graph launch");
+  }
+  c->launches += (n - 1) * c->graph_launches;
+  c->opt_steps += n - 1;
+  c->fwd_valid = false;
+  c->have_eval = true;
+  return cuda_check(c, cudaGetLastError(), "step graph");
+}
 cpra_status cpra_forward(cpra_ctx* c, const float* theta_dev, const float* emb_dev, float gamma,
                          float* terms_dev) {
   if (!c || !theta_dev || !emb_dev || !terms_dev)
@@ -895,10 +980,13 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
     best_out[s].violations = 0;
     best_out[s].qubo = 0.0;
   }
-  for (int64_t t = 0; t < steps; ++t) {
-    cpra_status st = cpra_step(c, t, nullptr);
+  for (int64_t t = 0; t < steps;) {
+    // steps t .. t_eval in one call (a captured step replayed), then evaluate
+    int64_t t_eval = (t == 0) ? 0 : std::min(steps - 1, (t + eval_every - 1) / eval_every * eval_every);
+    cpra_status st = cpra_steps(c, t, t_eval - t + 1);
     if (st != CPRA_OK) return st;
-    if (t % eval_every == 0 || t == steps - 1) {
+    t = t_eval + 1;
+    {
       st = cpra_round_eval(c, cur.data(), nullptr, nullptr);
       if (st != CPRA_OK) return st;
       st = check_err_flag(c);
@@ -907,7 +995,7 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
         const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
         if (ok && cur[s].objective > best_out[s].objective) {
           best_out[s] = cur[s];
-          best_step[s] = t;
+          best_step[s] = t_eval;
         }
       }
       if (c->cfg.es_patience > 0) {
@@ -1172,6 +1260,7 @@ void cpra_destroy(cpra_ctx* c) {
     if (r.a) cudaEventDestroy(r.a);
     if (r.b) cudaEventDestroy(r.b);
   }
+  drop_graph(c);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1183,6 +1272,7 @@ cpra_status cpra_set_init_logits(cpra_ctx* c, const float* logits, int64_t ld, i
   cudaStream_t st = c->stream;
   c->fwd_valid = false;
   c->have_eval = false;
+  drop_graph(c);  // the captured step carries the offset pointer
   if (!logits) {  // back to the plain network
     cpra_status s = cuda_check(c, cudaStreamSynchronize(st), "sync");
     if (c->init_logits) cudaFree(c->init_logits);

@@ -78,7 +78,7 @@ template <int LPR, int CPL, int PROBLEM, typename TG>
 __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int sub, unsigned smask,
                                              const float (&p)[CPL][4], const float (&q)[CPL][4],
                                              float deg, const float (&lam)[CPL][4],
-                                             ShotAcc<CPL>& acc) {
+                                             float gamma, ShotAcc<CPL>& acc) {
   const int S = a.S;
   const int nchG = (int)(a.ldg / 4);
   // Row statistics over the S shots: Psi is reported even when nu = 0.
@@ -116,7 +116,7 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
   } else {
     if (sub == 0) acc.psi += -(float)S * (float)S * var;
   }
-  const float c_ann = -2.f * (float)a.alpha * a.gamma;
+  const float c_ann = -2.f * (float)a.alpha * gamma;
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int ch = c * LPR + sub;
@@ -244,6 +244,7 @@ loss_kernel(LossArgs a) {
   const float* __restrict__ P = a.P;
   extern __shared__ float red[];  // [nwarps][S]
 
+  const float gamma = a.sc ? a.sc->gamma : a.gamma;
   float lam[CPL][4];
   if constexpr (DO_LOSS) load_lambda<LPR, CPL, PROBLEM>(a, sub, lam);
   ShotAcc<CPL> acc;
@@ -314,7 +315,8 @@ loss_kernel(LossArgs a) {
         }
       }
     }
-    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, acc);
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, gamma,
+                                        acc);
   }
   if constexpr (DO_LOSS) block_reduce<LPR, CPL>(a, acc, red);
 }
@@ -385,6 +387,7 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
   }
   __syncwarp();
 
+  const float gamma = a.sc ? a.sc->gamma : a.gamma;
   float lam[CPL][4];
   load_lambda<LPR, CPL, PROBLEM>(a, sub, lam);
   ShotAcc<CPL> acc;
@@ -503,7 +506,8 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
       }
     }
     if (a.xbits) store_bits<LPR, CPL>(a, i, sub, smask, p);
-    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, acc);
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, gamma,
+                                        acc);
   }
   if (dead) {
     if (lane == 0 && a.err_flag) atomicOr(a.err_flag, 2);

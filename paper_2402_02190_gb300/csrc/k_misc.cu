@@ -11,8 +11,12 @@ namespace {
 __global__ void adam_kernel(int64_t n, float* __restrict__ th, float* __restrict__ m,
                             float* __restrict__ v, const float* __restrict__ g, float lr,
                             float b1, float b2, float eps, float wd, float bc1, float bc2,
-                            const int* halt) {
+                            const int* halt, const StepScalars* sc) {
   if (halt && *halt) return;  // early stopping froze the parameters
+  if (sc) {
+    bc1 = sc->bc1;
+    bc2 = sc->bc2;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float mi = m[i], vi = v[i];
@@ -118,9 +122,9 @@ inline unsigned grid_for(int64_t n) {
 
 void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g, float lr,
                  float beta1, float beta2, float eps, float wd, float bc1, float bc2,
-                 const int* halt, cudaStream_t st) {
+                 const int* halt, const StepScalars* sc, cudaStream_t st) {
   adam_kernel<<<grid_for(n), 256, 0, st>>>(n, theta, m, v, g, lr, beta1, beta2, eps, wd, bc1,
-                                           bc2, halt);
+                                           bc2, halt, sc);
 }
 
 namespace {
@@ -128,9 +132,11 @@ namespace {
 // Single thread: the sums run in a fixed order with explicit roundings (no
 // contraction into fused multiply-adds), so the decision is reproducible.
 __global__ void early_stop_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
-                                  int S, float gamma, float tol, int patience, long long t,
-                                  long long updates, EarlyStopState* st) {
+                                  int S, float tol, int patience, const StepScalars* sc,
+                                  EarlyStopState* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0 || st->stopped) return;
+  const float gamma = sc->gamma;
+  const long long t = sc->t, updates = sc->updates;
   double l = 0.0, ann = 0.0;
   for (int s = 0; s < S; ++s) {
     double ls = (double)terms[s];
@@ -156,10 +162,48 @@ __global__ void early_stop_kernel(const float* __restrict__ terms, const float* 
 
 }  // namespace
 
-void early_stop_launch(const float* terms, const float* lambda, int S, float gamma, float tol,
-                       int patience, long long t, long long updates, EarlyStopState* st,
-                       cudaStream_t stream) {
-  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, gamma, tol, patience, t, updates, st);
+void early_stop_launch(const float* terms, const float* lambda, int S, float tol, int patience,
+                       const StepScalars* sc, EarlyStopState* st, cudaStream_t stream) {
+  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, tol, patience, sc, st);
+}
+
+namespace {
+
+// The linear schedule gamma_t = gamma0 + (gamma1 - gamma0) * min(t, T-1) / (T-1)
+// (one thread, explicit double roundings) and the Adam bias corrections
+// 1 - beta^(updates + 1).
+__global__ void step_scalars_kernel(StepScalars* sc, int from_device, long long t, long long updates,
+                                    float gamma0, float gamma1, long long T, float beta1,
+                                    float beta2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (from_device) {
+    t = sc->next_t;
+    updates = sc->next_updates;
+  }
+  float g = gamma1;
+  if (T > 1) {
+    long long tt = t < 0 ? 0 : (t > T - 1 ? T - 1 : t);
+    const double span = __dadd_rn((double)gamma1, -(double)gamma0);
+    const double frac = __ddiv_rn(__dmul_rn(span, (double)tt), (double)(T - 1));
+    g = (float)__dadd_rn((double)gamma0, frac);
+  }
+  const double u = (double)(updates + 1);
+  sc->gamma = g;
+  sc->bc1 = (float)(1.0 - pow((double)beta1, u));
+  sc->bc2 = (float)(1.0 - pow((double)beta2, u));
+  sc->t = t;
+  sc->updates = updates;
+  sc->next_t = t + 1;
+  sc->next_updates = updates + 1;
+}
+
+}  // namespace
+
+void step_scalars_launch(StepScalars* sc, int from_device, long long t, long long updates,
+                         float gamma0, float gamma1, long long T, float beta1, float beta2,
+                         cudaStream_t st) {
+  step_scalars_kernel<<<1, 32, 0, st>>>(sc, from_device, t, updates, gamma0, gamma1, T, beta1,
+                                        beta2);
 }
 
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd, int ddst,

@@ -51,7 +51,14 @@ spmm_rows_kernel(SpmmArgs a) {
   const TX* __restrict__ MASK = static_cast<const TX*>(a.mask);
   const uint64_t pol = l2_evict_first_policy();
   bool update = true;  // embedding Adam step (ADAM kind), off once early stopping fired
-  if constexpr (ADAM) update = !(a.halt && *a.halt);
+  float bc1 = a.bc1, bc2 = a.bc2;
+  if constexpr (ADAM) {
+    update = !(a.halt && *a.halt);
+    if (a.sc) {
+      bc1 = a.sc->bc1;
+      bc2 = a.sc->bc2;
+    }
+  }
 
   float csum[CPL][VEC];
 #pragma unroll
@@ -193,7 +200,7 @@ spmm_rows_kernel(SpmmArgs a) {
 #pragma unroll
           for (int v = 0; v < VEC; ++v)
             th[v] = adam_update(th[v], m[v], vv[v], o[v], a.lr, a.beta1, a.beta2, a.eps, a.wd,
-                                a.bc1, a.bc2);
+                                bc1, bc2);
           storeN_stream<VEC>(a.emb + off, th, pol);
           storeN_stream<VEC>(a.emb_m + off, m, pol);
           storeN_stream<VEC>(a.emb_v + off, vv, pol);

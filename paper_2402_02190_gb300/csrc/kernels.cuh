@@ -9,6 +9,24 @@ namespace cpra {
 
 enum DType { DT_F32 = 0, DT_BF16 = 1 };
 
+// Per-step scalars of a training step, computed on the device by
+// step_scalars_launch so that a step's launches carry no per-step host
+// arguments (the step can be captured once and replayed): the annealing
+// weight gamma_t of the linear schedule and the Adam bias corrections for
+// the step's update.  t / updates are the step's schedule index and the
+// number of updates before it; next_t / next_updates are what the following
+// step takes when it reads them from here.
+struct StepScalars {
+  float gamma, bc1, bc2;
+  int pad;
+  long long t, updates;
+  long long next_t, next_updates;
+};
+// from_device = 0: the step is (t, updates); 1: it is (next_t, next_updates).
+void step_scalars_launch(StepScalars* sc, int from_device, long long t, long long updates,
+                         float gamma0, float gamma1, long long T, float beta1, float beta2,
+                         cudaStream_t st);
+
 // ---------------------------------------------------------------- SpMM
 // Row-gather SpMM over the symmetric CSR (Eq. GCN aggregate step):
 //   Y_i = s_i * (add_i + sum_{j in N(i)} X_j)  [* 1[mask_i > 0]]
@@ -45,6 +63,7 @@ struct SpmmArgs {
   // dx, row stride lds).  Y may be null (the gradient is then not stored).
   int adam = 0;
   const int* halt = nullptr;  // while *halt != 0 the embedding rows are left as they are
+  const StepScalars* sc = nullptr;  // when set, bc1 / bc2 are sc->bc1 / sc->bc2
   float* emb = nullptr;
   float* emb_m = nullptr;
   float* emb_v = nullptr;
@@ -73,6 +92,7 @@ struct LossArgs {
   const float* lambda = nullptr;
   int problem = 0, alpha = 2, div_kind = 0, grad_kind = 0;
   float gamma = 0.f, nu = 0.f;
+  const StepScalars* sc = nullptr;  // when set, gamma is sc->gamma
   void* G = nullptr;             // dtype dg, N x ldg
   int dg = DT_F32;
   uint32_t* xbits = nullptr;     // N x W, W = ceil(S/32)
@@ -157,9 +177,11 @@ void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp,
 
 // ---------------------------------------------------------------- misc
 // Adam on n parameters; skipped entirely while *halt != 0 (halt may be null).
+// With sc non-null the bias corrections are sc->bc1, sc->bc2.
 void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g,
                  float lr, float beta1, float beta2, float eps, float wd,
-                 float bc1, float bc2, const int* halt, cudaStream_t st);
+                 float bc1, float bc2, const int* halt, const StepScalars* sc,
+                 cudaStream_t st);
 
 // Early-stopping monitor (Implementation paragraph), one thread: from the
 // step's loss terms (cost S | pen S | ann S) forms l = sum_s (cost_s +
@@ -178,9 +200,9 @@ struct EarlyStopState {
   int stopped;                // halts the parameter updates
   int pad;
 };
-void early_stop_launch(const float* terms, const float* lambda, int S, float gamma, float tol,
-                       int patience, long long t, long long updates, EarlyStopState* st,
-                       cudaStream_t stream);
+// gamma, t and updates are the step's, read from sc.
+void early_stop_launch(const float* terms, const float* lambda, int S, float tol, int patience,
+                       const StepScalars* sc, EarlyStopState* st, cudaStream_t stream);
 // ---------------------------------------------------------------- warm start (k_warm.cu)
 // Node features [N x F]: 1, deg/8, then N(0,1) from the stream of `seed`.
 void ws_features_launch(int64_t N, const int* rowptr, uint64_t seed, int F, float* out,

@@ -369,7 +369,7 @@ cpra_status cpra_ws_train_step(cpra_ws* w, int64_t N, int64_t nnz, const int32_t
   const float bc1 = (float)(1.0 - std::pow((double)w->cfg.beta1, t));
   const float bc2 = (float)(1.0 - std::pow((double)w->cfg.beta2, t));
   adam_launch(w->nstore, w->theta, w->m, w->v, w->grad, w->cfg.lr, w->cfg.beta1, w->cfg.beta2,
-              w->cfg.eps, w->cfg.weight_decay, bc1, bc2, nullptr, st);
+              w->cfg.eps, w->cfg.weight_decay, bc1, bc2, nullptr, nullptr, st);
   ws_shadows(w);
   if (cudaGetLastError() != cudaSuccess) return ws_fail(w, CPRA_ECUDA, "training kernels");
   if (loss_out) {
