@@ -53,6 +53,7 @@ import numpy as np
 
 MIS = 0
 MAXCUT = 1
+WMIS = 2   # weighted MIS (App. two-stage experiment): weight w_is of node i in task s
 DIV_STD = 0
 DIV_VAR = 1
 
@@ -185,12 +186,14 @@ def shot_variance(P: np.ndarray) -> np.ndarray:
     return ((P - m[:, None]) ** 2).sum(axis=1) / S
 
 
-def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD):
+def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None):
     """Per-shot cost_s, pen_s, ann_s and the shot-coupling Psi.
 
     MIS    l = -sum_i p_i + lambda sum_{(i,j) in E} p_i p_j
            cost_s = -sum_i P_is, pen_s = sum_{(i,j) in E} P_is P_js
     MaxCut l = sum_{i<j} A_ij (2 p_i p_j - p_i - p_j); cost_s = l, pen_s = 0
+    WMIS   l = -sum_i w_i p_i + lambda sum_{(i,j) in E} p_i p_j (task s has its
+           own node weights w_:s); cost_s = -sum_i w_is P_is, pen_s as MIS
     ann_s  = sum_i 1 - (2 P_is - 1)^alpha
     Psi    = -S sum_i STD_s[P_is]        (STD form, Eq. ...-variation)
            = -S^2 sum_i VAR_s[P_is]      (VAR form, Prop. 3.2 left-hand side)
@@ -200,6 +203,9 @@ def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD):
     Pi, Pj = P[g.ei], P[g.ej]
     if problem == MIS:
         cost = -P.sum(axis=0)
+        pen = (Pi * Pj).sum(axis=0)
+    elif problem == WMIS:
+        cost = -(np.asarray(weights, dtype=np.float64) * P).sum(axis=0)
         pen = (Pi * Pj).sum(axis=0)
     elif problem == MAXCUT:
         cost = (g.ew[:, None] * (2.0 * Pi * Pj - Pi - Pj)).sum(axis=0)
@@ -220,19 +226,19 @@ def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD):
 def total_loss(terms, lam, gamma, nu, problem):
     lam = np.asarray(lam, dtype=np.float64)
     base = terms["cost"].sum()
-    if problem == MIS:
+    if problem in (MIS, WMIS):
         base += (lam * terms["pen"]).sum()
     return base + gamma * terms["ann"].sum() + nu * terms["psi"]
 
 
-def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD):
+def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD, weights=None):
     """dR/dP_is, analytic, with the edge list traversed once per edge."""
     P = np.asarray(P, dtype=np.float64)
     N, S = P.shape
     G = np.zeros((N, S))
-    if problem == MIS:
+    if problem in (MIS, WMIS):
         lam = np.asarray(lam, dtype=np.float64)
-        G -= 1.0
+        G -= 1.0 if problem == MIS else np.asarray(weights, dtype=np.float64)
         np.add.at(G, g.ei, lam[None, :] * P[g.ej])
         np.add.at(G, g.ej, lam[None, :] * P[g.ei])
     else:
@@ -347,25 +353,32 @@ def round_solutions(P) -> np.ndarray:
     return (np.asarray(P) > 0.5).astype(np.int64)
 
 
-def integer_eval(g: Graph, X, lam, problem):
+def integer_eval(g: Graph, X, lam, problem, weights=None):
     """Per shot: objective (MIS set size / MaxCut cut size), violations
-    (MIS: edges with both ends selected; MaxCut: 0), qubo value l(x), and
-    the pairwise Hamming sum sum_{s<l} d_H(x_s, x_l)."""
+    (MIS: edges with both ends selected; MaxCut: 0), qubo value l(x), the
+    objective in the problem's own units `value` (set size, total weight of
+    the set for weighted MIS, cut size), and the pairwise Hamming sum
+    sum_{s<l} d_H(x_s, x_l)."""
     X = np.asarray(X, dtype=np.int64)
     N, S = X.shape
     Xi, Xj = X[g.ei], X[g.ej]
-    if problem == MIS:
+    if problem in (MIS, WMIS):
         obj = X.sum(axis=0)
         viol = (Xi * Xj).sum(axis=0)
-        qubo = -obj.astype(np.float64) + np.asarray(lam, np.float64) * viol
+        value = obj.astype(np.float64)
+        if problem == WMIS:
+            value = (np.asarray(weights, dtype=np.float64) * X).sum(axis=0)
+        qubo = -value + np.asarray(lam, np.float64) * viol
     else:
         obj = (Xi != Xj).sum(axis=0)
         viol = np.zeros(S, dtype=np.int64)
         qubo = -(g.ew[:, None] * (Xi != Xj)).sum(axis=0)
+        value = obj.astype(np.float64)
     k = X.sum(axis=1)
     pair_hamming = int((k * (S - k)).sum())
     return dict(objective=obj.astype(np.int64), violations=viol.astype(np.int64),
-                qubo=qubo.astype(np.float64), pair_hamming=pair_hamming)
+                qubo=qubo.astype(np.float64), value=np.asarray(value, np.float64),
+                pair_hamming=pair_hamming)
 
 
 def pack_bits(X) -> np.ndarray:
@@ -387,15 +400,18 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
     """One CPRA step at iteration t (1-based for Adam bias correction).
 
     cfg keys: H0, H1, S, problem, alpha, lam (S), gamma, nu, div_kind,
-    lr, beta1, beta2, eps, wd, train_embedding.
+    lr, beta1, beta2, eps, wd, train_embedding, optional weights (N x S,
+    weighted MIS) and train_encoder (False: only the head Wcat2, b2 is
+    updated, as in the fine-tuning stage of the two-stage schedule).
     adam_state: dict(m_theta, v_theta, m_X0, v_X0) or None (zeros)."""
     H0, H1, S = cfg["H0"], cfg["H1"], cfg["S"]
     cache = forward(g, theta, X0, H0, H1, S, cfg.get("relu_decision"), cfg.get("init_logits"))
     P = cache["P"]
-    terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"])
+    W = cfg.get("weights")
+    terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"], W)
     L = total_loss(terms, cfg["lam"], cfg["gamma"], cfg["nu"], cfg["problem"])
     G_P = grad_P(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["gamma"],
-                 cfg["nu"], cfg["div_kind"])
+                 cfg["nu"], cfg["div_kind"], W)
     grads = backward(g, theta, cache, G_P, H0, H1, S)
     if adam_state is None:
         adam_state = dict(m_theta=np.zeros(len(theta)), v_theta=np.zeros(len(theta)),
@@ -404,14 +420,20 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
               wd=cfg["wd"])
     th1, mt, vt = adam(theta, adam_state["m_theta"], adam_state["v_theta"],
                        grads["theta"], t, **hp)
-    if cfg.get("train_embedding", True):
+    encoder = cfg.get("train_encoder", True)
+    if not encoder:  # head only: layer-1 weights and the embeddings keep their values
+        h0 = 2 * H1 * H0 + H1
+        th1[:h0] = np.asarray(theta, np.float64)[:h0]
+        mt[:h0] = np.asarray(adam_state["m_theta"], np.float64)[:h0]
+        vt[:h0] = np.asarray(adam_state["v_theta"], np.float64)[:h0]
+    if cfg.get("train_embedding", True) and encoder:
         x1, mx, vx = adam(X0, adam_state["m_X0"], adam_state["v_X0"], grads["X0"], t, **hp)
     else:
         x1 = np.asarray(X0, np.float64)
         mx = np.asarray(adam_state["m_X0"], np.float64)
         vx = np.asarray(adam_state["v_X0"], np.float64)
     X = round_solutions(P)
-    ev = integer_eval(g, X, cfg["lam"], cfg["problem"])
+    ev = integer_eval(g, X, cfg["lam"], cfg["problem"], W)
     return dict(cache=cache, P=P, terms=terms, loss=L, G_P=G_P, grads=grads,
                 theta_next=th1, X0_next=x1,
                 adam_next=dict(m_theta=mt, v_theta=vt, m_X0=mx, v_X0=vx),
