@@ -54,7 +54,10 @@ typedef enum {
   CPRA_ESTATE = 6    /* state blob does not match this context             */
 } cpra_status;
 
-enum { CPRA_MIS = 0, CPRA_MAXCUT = 1 };               /* Table objective-functions */
+enum { CPRA_MIS = 0, CPRA_MAXCUT = 1,                 /* Table objective-functions */
+       CPRA_WMIS = 2 };  /* weighted MIS: shot s solves the MIS QUBO with node weights
+                            w_:s (the task family of the paper's two-stage experiment);
+                            weights from cpra_set_node_weights, 1 until set */
 enum { CPRA_FP32 = 0, CPRA_BF16 = 1 };                /* dense-layer arithmetic   */
 enum { CPRA_DIV_STD = 0, CPRA_DIV_VAR = 1 };          /* Psi form                 */
 
@@ -98,14 +101,23 @@ typedef struct cpra_config {
                                it and every later cpra_step leave parameters
                                and Adam state unchanged                      */
   int32_t es_patience;      /* 0: no early stopping                             */
+  float es_ann_below;       /* > 0: a step whose annealing term sum_s ann_s is
+                               below this value also stops the run (the two-stage
+                               experiment's rule); 0: off                       */
+  int32_t train_encoder;    /* 1 (default): all parameters train; 0: only the
+                               head [B2|W2], b2 trains (the fine-tuning stage of
+                               the two-stage schedule); layer 1 and the
+                               embeddings keep their values                    */
 } cpra_config;
 
 /* Result of rounding one shot (App. C.2) and evaluating it exactly. */
 typedef struct cpra_shot_eval {
-  int64_t objective;   /* MIS: |{i : x_i = 1}|;  MaxCut: number of cut edges   */
-  int64_t violations;  /* MIS: edges with both ends in the set; MaxCut: 0      */
-  double qubo;         /* l(x): MIS -objective + lambda_s * violations;
-                          MaxCut -objective                                     */
+  int64_t objective;   /* (W)MIS: |{i : x_i = 1}|;  MaxCut: number of cut edges */
+  int64_t violations;  /* (W)MIS: edges with both ends in the set; MaxCut: 0     */
+  double qubo;         /* l(x): -value + lambda_s * violations ((W)MIS);
+                          -value (MaxCut)                                       */
+  double value;        /* objective in the problem's units: set size, total
+                          weight sum_i w_is x_is (WMIS, FP64), cut size      */
 } cpra_shot_eval;
 
 typedef struct cpra_ctx cpra_ctx;
@@ -113,7 +125,8 @@ typedef struct cpra_ctx cpra_ctx;
 /* Fills *cfg with defaults: MIS, S = 8, H0 = H1 = 16, alpha = 2, FP32,
    recompute 0, train_embedding 1, keep_emb_grad 0, DIV_STD, nu = 0,
    gamma -2 -> 0.1 over 3000 steps, Adam lr 1e-3, betas (0.9, 0.999),
-   eps 1e-8, wd 0, seed 1, no early stopping (es_patience 0, es_tol 1e-5). */
+   eps 1e-8, wd 0, seed 1, no early stopping (es_patience 0, es_tol 1e-5,
+   es_ann_below 0), train_encoder 1. */
 CPRA_API void cpra_config_default(cpra_config* cfg);
 
 /* Number of trainable GNN parameters excluding node embeddings:
@@ -192,6 +205,13 @@ CPRA_API cpra_status cpra_round_eval(cpra_ctx* ctx, cpra_shot_eval* out,
    parameters are frozen from the stopping step on). */
 CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every,
                        cpra_shot_eval* best_out, int64_t* best_step_out);
+
+/* Weighted MIS (problem CPRA_WMIS): node weights w [N x ld] float (ld >= S),
+   w_is for node i in shot s, on the host (on_device = 0) or the current
+   device (on_device = 1); copied into the context's workspace.
+   Synchronises.  Errors: CPRA_EINVAL (not a WMIS context, NULL, ld < S). */
+CPRA_API cpra_status cpra_set_node_weights(cpra_ctx* ctx, const float* w, int64_t ld,
+                                           int32_t on_device);
 
 /* Schedule index t of the cpra_step at which early stopping fired, or -1
    (also when es_patience is 0).  Synchronises. */

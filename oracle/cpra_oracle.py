@@ -310,7 +310,7 @@ def gamma_schedule(t, T, gamma0, gamma1):
     return gamma0 + (gamma1 - gamma0) * min(t, T - 1) / (T - 1)
 
 
-def early_stop_step(terms_seq, gammas, lam, problem, tol, patience):
+def early_stop_step(terms_seq, gammas, lam, problem, tol, patience, ann_below=0.0):
     """Early stopping of the Implementation paragraph: the run is monitored
     through the summed penalty-form loss l_t = sum_s (cost_s + lambda_s pen_s)
     (MaxCut: sum_s cost_s) and the annealing term phi_t = gamma_t sum_s ann_s,
@@ -319,6 +319,10 @@ def early_stop_step(terms_seq, gammas, lam, problem, tol, patience):
     from step t-1 is positive or at most `tol` in magnitude; the run stops at
     the step that completes `patience` consecutive stale steps.  Sums run over
     s = 0..S-1 in order, in float64, from the per-step terms as given.
+
+    With ann_below > 0, a step whose annealing sum sum_s ann_s is below it
+    stops the run as well (the stopping rule of the two-stage experiment,
+    App. two-stage); patience 0 disables the stale-step rule.
 
     terms_seq: per step (cost[S], pen[S], ann[S]); gammas: per step gamma_t.
     Returns the index of the stopping step, or -1."""
@@ -329,12 +333,14 @@ def early_stop_step(terms_seq, gammas, lam, problem, tol, patience):
         a_t = 0.0
         for s in range(len(cost)):
             ls = float(cost[s])
-            if problem == MIS:
+            if problem in (MIS, WMIS):
                 ls = ls + float(lam[s]) * float(pen[s])
             l_t = l_t + ls
             a_t = a_t + float(ann[s])
         phi_t = float(gamma) * a_t
-        if prev is not None:
+        if ann_below > 0.0 and a_t < ann_below:
+            return t
+        if patience > 0 and prev is not None:
             dl = l_t - prev[0]
             dp = phi_t - prev[1]
             stale = (dl > 0.0 or abs(dl) <= tol) and (dp > 0.0 or abs(dp) <= tol)

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libcpra.so")
 
 CPRA_OK, CPRA_EINVAL, CPRA_ENOMEM, CPRA_ECUDA, CPRA_ENUMERIC, CPRA_ETIMEOUT, CPRA_ESTATE = range(7)
-MIS, MAXCUT = 0, 1
+MIS, MAXCUT, WMIS = 0, 1, 2
 FP32, BF16 = 0, 1
 DIV_STD, DIV_VAR = 0, 1
 (T_THETA, T_THETA_M, T_THETA_V, T_EMB, T_EMB_M, T_EMB_V, T_GRAD, T_EMB_GRAD, T_P, T_GZ2,
@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
     "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
-    "cpra_set_init_logits", "cpra_steps", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
+    "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
     "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
     "cpra_ws_set_params", "cpra_ws_destroy",
 )
@@ -56,7 +56,8 @@ class Config(C.Structure):
         ("gamma1", C.c_float), ("schedule_steps", C.c_int64), ("lr", C.c_float),
         ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
         ("weight_decay", C.c_float), ("seed", C.c_uint64), ("mem_cap_bytes", C.c_uint64),
-        ("es_tol", C.c_float), ("es_patience", C.c_int32),
+        ("es_tol", C.c_float), ("es_patience", C.c_int32), ("es_ann_below", C.c_float),
+        ("train_encoder", C.c_int32),
     ]
 
 
@@ -69,10 +70,12 @@ class WsConfig(C.Structure):
 
 
 class ShotEval(C.Structure):
-    _fields_ = [("objective", C.c_int64), ("violations", C.c_int64), ("qubo", C.c_double)]
+    _fields_ = [("objective", C.c_int64), ("violations", C.c_int64), ("qubo", C.c_double),
+                ("value", C.c_double)]
 
 
-SHOT_EVAL_DTYPE = np.dtype([("objective", "<i8"), ("violations", "<i8"), ("qubo", "<f8")])
+SHOT_EVAL_DTYPE = np.dtype([("objective", "<i8"), ("violations", "<i8"), ("qubo", "<f8"),
+                            ("value", "<f8")])
 
 _lib = None
 
@@ -108,6 +111,7 @@ def lib():
         "cpra_launch_count": (i64, [vp]),
         "cpra_early_stop_step": (i64, [vp]),
         "cpra_steps": (i32, [vp, i64, i64]),
+        "cpra_set_node_weights": (i32, [vp, vp, i64, i32]),
         "cpra_set_init_logits": (i32, [vp, vp, i64, i32]),
         "cpra_profile_enable": (None, [vp, C.c_int]),
         "cpra_profile_read": (i32, [vp, vp, vp, i32]),
@@ -306,6 +310,16 @@ def cpra_launch_count(ctx) -> int:
     return int(lib().cpra_launch_count(ctx))
 
 
+def cpra_set_node_weights(ctx, w) -> None:
+    """Weighted MIS node weights: a host array [N, S] or a CUDA tensor [N, S]."""
+    if hasattr(w, "is_cuda") and w.is_cuda:
+        t = w.float().contiguous()
+        _check(lib().cpra_set_node_weights(ctx, C.c_void_p(t.data_ptr()), t.shape[1], 1), ctx)
+        return
+    a = np.ascontiguousarray(w, dtype=np.float32)
+    _check(lib().cpra_set_node_weights(ctx, _ptr(a), a.shape[1], 0), ctx)
+
+
 def cpra_steps(ctx, t0: int, n: int) -> None:
     _check(lib().cpra_steps(ctx, int(t0), int(n)), ctx)
 
@@ -332,7 +346,7 @@ def paper_preset(problem: int, max_steps: int = 50_000) -> dict:
     paragraph): AdamW lr 1e-4, weight decay 1e-2; gamma(0) = -20 for MIS and
     -6 for MaxCut rising by 1e-3 per step (a linear schedule over max_steps);
     alpha = 2; early stopping with tolerance 1e-5 and patience 1000."""
-    g0 = -20.0 if problem == MIS else -6.0
+    g0 = -6.0 if problem == MAXCUT else -20.0
     return dict(lr=1e-4, weight_decay=1e-2, gamma0=g0, gamma1=g0 + 1e-3 * (max_steps - 1),
                 schedule_steps=max_steps, alpha=2, es_tol=1e-5, es_patience=1000)
 
@@ -400,6 +414,8 @@ def cpra_op_round_eval_scratch_bytes(S: int) -> int:
 def cpra_op_round_eval(rowptr32, col32, P, S, lam, problem, x_bits, out_records, pair_hamming,
                        counters, stream=None):
     N = P.shape[0]
+    if out_records.numel() * out_records.element_size() < S * SHOT_EVAL_DTYPE.itemsize:
+        raise ValueError("out_records holds fewer than S cpra_shot_eval records")
     st = lib().cpra_op_round_eval(
         N, S, C.c_void_p(rowptr32.data_ptr()), C.c_void_p(col32.data_ptr()),
         C.c_void_p(P.data_ptr()), P.stride(0),
@@ -432,6 +448,12 @@ class Solver:
 
     def solve(self, steps: int, eval_every: int):
         return cpra_solve(self.ctx, steps, eval_every)
+
+    def set_node_weights(self, w) -> None:
+        if hasattr(w, "is_cuda") and w.is_cuda:
+            import torch
+            self.stream.wait_stream(torch.cuda.current_stream())
+        cpra_set_node_weights(self.ctx, w)
 
     def steps(self, t0: int, n: int) -> None:
         cpra_steps(self.ctx, t0, n)

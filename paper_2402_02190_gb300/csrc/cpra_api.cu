@@ -54,6 +54,7 @@ const char* kKernelNames[K_COUNT_] = {
     "recompute_layer1_mask"};
 
 constexpr size_t kAlign = 256;
+constexpr int kWvBlocks = 512;  // weighted-MIS value partial rows
 
 struct Carver {
   char* base;
@@ -119,6 +120,10 @@ struct cpra_ctx {
   void* GXM = nullptr;   // aliases XM when recompute
   uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
   EarlyStopState* es = nullptr;   // early-stopping monitor (device)
+  float* w_d = nullptr;           // weighted MIS: node weights N x S_pad (else null)
+  double* wv_part = nullptr;      // weighted MIS: per-block value partials
+  double* wvalue = nullptr;       // weighted MIS: per-shot value
+  bool wmis = false;
   void* init_logits = nullptr;    // warm start: N x S_pad act dtype, own cudaMalloc
   StepScalars* sc = nullptr;      // per-step gamma / bias corrections (device)
   // one captured training step, replayed by cpra_steps / cpra_solve
@@ -186,7 +191,8 @@ Layout layout_of(int H0, int H1, int S) {
 
 std::string validate_config(const cpra_config* cfg) {
   if (!cfg) return "cfg is NULL";
-  if (cfg->problem != CPRA_MIS && cfg->problem != CPRA_MAXCUT) return "problem must be MIS or MAXCUT";
+  if (cfg->problem != CPRA_MIS && cfg->problem != CPRA_MAXCUT && cfg->problem != CPRA_WMIS)
+    return "problem must be MIS, MAXCUT or WMIS";
   if (cfg->S < 1 || cfg->S > 1024) return "S must be in [1, 1024]";
   if (cfg->H0 < 16 || cfg->H0 > 1024 || cfg->H0 % 16) return "H0 must be a multiple of 16 in [16, 1024]";
   if (cfg->H1 < 16 || cfg->H1 > 1024 || cfg->H1 % 16) return "H1 must be a multiple of 16 in [16, 1024]";
@@ -197,7 +203,10 @@ std::string validate_config(const cpra_config* cfg) {
   if (cfg->recompute != 0 && cfg->recompute != 1) return "recompute must be 0 or 1";
   if (cfg->es_patience < 0 || !(cfg->es_tol >= 0.f) || !std::isfinite(cfg->es_tol))
     return "early stopping needs es_patience >= 0 and a finite es_tol >= 0";
-  if (cfg->problem == CPRA_MIS && cfg->lambda == nullptr) return "MIS needs lambda[S]";
+  if (cfg->problem != CPRA_MAXCUT && cfg->lambda == nullptr) return "MIS needs lambda[S]";
+  if (cfg->train_encoder != 0 && cfg->train_encoder != 1) return "train_encoder must be 0 or 1";
+  if (!(cfg->es_ann_below >= 0.f) || !std::isfinite(cfg->es_ann_below))
+    return "es_ann_below must be finite and >= 0";
   if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
   if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
       !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps >= 0.f) || !(cfg->weight_decay >= 0.f))
@@ -280,6 +289,15 @@ size_t carve(cpra_ctx* c, void* base) {
   c->wg_part = cv.take<float>(c->wg_part_floats);
   c->err_flag = cv.take<int>(4);
   c->es = cv.take<EarlyStopState>(1);
+  if (c->wmis) {
+    c->w_d = cv.take<float>((size_t)N * c->S_pad);
+    c->wv_part = cv.take<double>((size_t)kWvBlocks * c->S);
+    c->wvalue = cv.take<double>(c->S);
+  } else {
+    c->w_d = nullptr;
+    c->wv_part = nullptr;
+    c->wvalue = nullptr;
+  }
   c->sc = cv.take<StepScalars>(1);
   c->W1s = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W1t = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
@@ -299,6 +317,7 @@ void set_dims(cpra_ctx* c, int64_t N, int64_t nnz, const cpra_config* cfg) {
   c->act_dt = cfg->precision == CPRA_BF16 ? DT_BF16 : DT_F32;
   c->nparam = layout_of(cfg->H0, cfg->H1, cfg->S).total;
   c->recompute = cfg->recompute != 0;
+  c->wmis = cfg->problem == CPRA_WMIS;
 }
 
 // ---------------------------------------------------------------- profiling
@@ -357,9 +376,8 @@ cpra_status read_early_stop(cpra_ctx* c, EarlyStopState* h) {
   if (h->stopped) c->opt_steps = h->updates_at_stop;
   return CPRA_OK;
 }
-const int* halt_flag(const cpra_ctx* c) {
-  return c->cfg.es_patience > 0 ? &c->es->stopped : nullptr;
-}
+bool es_on(const cpra_ctx* c) { return c->cfg.es_patience > 0 || c->cfg.es_ann_below > 0.f; }
+const int* halt_flag(const cpra_ctx* c) { return es_on(c) ? &c->es->stopped : nullptr; }
 
 float gamma_at(const cpra_config& cfg, int64_t t) {
   if (cfg.schedule_steps <= 1) return cfg.gamma1;
@@ -476,7 +494,9 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     LossArgs a;
     a.N = N; a.S = c->S; a.ldp = c->S_pad; a.ldg = c->S_pad;
     a.rowptr = c->rowptr; a.col = c->col; a.P = c->P; a.lambda = c->lambda_d;
-    a.problem = c->cfg.problem; a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
+    a.problem = c->cfg.problem == CPRA_MAXCUT ? 1 : 0;  // weighted MIS: MIS with weights
+    a.w = c->w_d; a.ldw = c->S_pad;
+    a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
     a.grad_kind = 0; a.gamma = gamma; a.sc = do_loss ? sc : nullptr; a.nu = c->cfg.nu;
     a.G = c->GZ2; a.dg = c->act_dt; a.xbits = c->xbits;
     a.partials = c->loss_part; a.pstride = c->pstride; a.err_flag = c->err_flag;
@@ -494,10 +514,16 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     Region r(c, K_EVAL);
     cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
                     c->stream);
-    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits, c->cfg.problem, c->counters,
+    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits, c->cfg.problem == CPRA_MAXCUT ? 1 : 0,
+                     c->counters,
                      c->num_sms * 8, c->stream);
-    eval_finalize(c->counters, c->S, c->cfg.problem, c->lambda_d, c->eval_rec, c->ham_d,
-                  c->stream);
+    if (c->w_d) {  // weighted MIS: the value of each shot in weight units
+      weighted_value_launch(N, c->S, c->xbits, c->w_d, c->S_pad, c->wv_part, kWvBlocks,
+                            c->wvalue, c->stream);
+      c->launches += 2;
+    }
+    eval_finalize(c->counters, c->S, c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->lambda_d,
+                  c->eval_rec, c->ham_d, c->stream, c->w_d ? c->wvalue : nullptr);
     c->launches += 2;
   }
   c->have_eval = true;
@@ -526,6 +552,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     Region r(c, K_WGRAD2);  // dWcat2 = G_Z2^T [H1|M2]
     wgrad(c, c->GZ2, c->S_pad, c->S, c->HM, 2 * H1, 2 * H1, c->grad + L.wcat2, 2 * H1);
   }
+  if (!c->cfg.train_encoder) return CPRA_OK;  // head only: db2 and dWcat2 are all it needs
   {  // [G_H1a | G_M2/deg] = G_Z2 Wcat2
     Region r(c, K_GEMM_DGRAD2);
     GemmArgs g;
@@ -622,7 +649,10 @@ cpra_status run_update(cpra_ctx* c) {
   adam_bias(c, &bc1, &bc2);
   {
     Region r(c, K_ADAM);
-    adam_launch(c->nparam, c->theta, c->theta_m, c->theta_v, c->grad, c->cfg.lr, c->cfg.beta1,
+    // head only: Adam on the trailing [Wcat2 | b2] block; layer 1 keeps its values
+    const int64_t off = c->cfg.train_encoder ? 0 : layout_of(c->H0, c->H1, c->S).wcat2;
+    adam_launch(c->nparam - off, c->theta + off, c->theta_m + off, c->theta_v + off, c->grad + off,
+                c->cfg.lr, c->cfg.beta1,
                 c->cfg.beta2, c->cfg.eps, c->cfg.weight_decay, bc1, bc2, halt_flag(c), c->sc,
                 c->stream);
     c->launches += 1;
@@ -679,6 +709,8 @@ void cpra_config_default(cpra_config* cfg) {
   cfg->mem_cap_bytes = 0;
   cfg->es_tol = 1e-5f;
   cfg->es_patience = 0;
+  cfg->es_ann_below = 0.f;
+  cfg->train_encoder = 1;
 }
 
 int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S) {
@@ -783,6 +815,7 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   cudaMemsetAsync(c->err_flag, 0, sizeof(int) * 4, st);
   reset_early_stop(c);
   cudaMemsetAsync(c->terms, 0, sizeof(float) * (4 * c->S + 1), st);
+  if (c->w_d) fill_rows_launch(N, c->S, c->S_pad, 1.f, c->w_d, st);  // weights 1 until set
   // parameters: U(+-1/sqrt(fan_in)) for weights and biases, N(0,1) embeddings
   const Layout L = layout_of(c->H0, c->H1, c->S);
   const uint64_t seed = cfg->seed;
@@ -816,12 +849,13 @@ namespace {
 cpra_status launch_step_body(cpra_ctx* c) {
   cpra_status s = run_forward_and_loss(c, 0.f, true, c->sc);
   if (s != CPRA_OK) return s;
-  if (c->cfg.es_patience > 0) {
-    early_stop_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S,
-                      c->cfg.es_tol, c->cfg.es_patience, c->sc, c->es, c->stream);
+  if (es_on(c)) {
+    early_stop_launch(c->terms, c->cfg.problem != CPRA_MAXCUT ? c->lambda_d : nullptr, c->S,
+                      c->cfg.es_tol, c->cfg.es_patience, c->cfg.es_ann_below, c->sc, c->es,
+                      c->stream);
     c->launches += 1;
   }
-  const bool emb = c->cfg.train_embedding != 0;
+  const bool emb = c->cfg.train_embedding != 0 && c->cfg.train_encoder != 0;
   s = run_backward(c, emb, /*fuse_adam=*/emb);
   if (s != CPRA_OK) return s;
   return run_update(c);
@@ -928,7 +962,7 @@ cpra_status cpra_forward(cpra_ctx* c, const float* theta_dev, const float* emb_d
   refresh_emb_shadow(c);
   s = run_forward_and_loss(c, gamma, true);
   if (s != CPRA_OK) return s;
-  total_loss_launch(c->terms, c->cfg.problem == CPRA_MIS ? c->lambda_d : nullptr, c->S, gamma,
+  total_loss_launch(c->terms, c->cfg.problem != CPRA_MAXCUT ? c->lambda_d : nullptr, c->S, gamma,
                     c->cfg.nu, terms_dev, st);
   c->launches += 1;
   c->fwd_valid = true;
@@ -998,7 +1032,7 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
           best_step[s] = t_eval;
         }
       }
-      if (c->cfg.es_patience > 0) {
+      if (es_on(c)) {
         EarlyStopState h;
         st = read_early_stop(c, &h);
         if (st != CPRA_OK) return fail(c, st, "early-stopping state readback");
@@ -1059,7 +1093,7 @@ cpra_status cpra_get_tensor(cpra_ctx* c, int32_t which, void* host, size_t nbyte
   cpra_status s = CPRA_OK;
   if (which == CPRA_T_STEP) {
     s = cuda_check(c, cudaStreamSynchronize(st), "sync");
-    if (s == CPRA_OK && c->cfg.es_patience > 0) {
+    if (s == CPRA_OK && es_on(c)) {
       EarlyStopState h;
       s = read_early_stop(c, &h);
     }
@@ -1192,7 +1226,7 @@ int64_t cpra_param_count(const cpra_ctx* c) { return c ? c->nparam : 0; }
 int64_t cpra_launch_count(const cpra_ctx* c) { return c ? c->launches : 0; }
 
 int64_t cpra_early_stop_step(cpra_ctx* c) {
-  if (!c || c->cfg.es_patience <= 0) return -1;
+  if (!c || !es_on(c)) return -1;
   EarlyStopState h;
   if (read_early_stop(c, &h) != CPRA_OK) return -1;
   return h.stopped ? (int64_t)h.stop_step : -1;
@@ -1265,6 +1299,24 @@ void cpra_destroy(cpra_ctx* c) {
   if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+cpra_status cpra_set_node_weights(cpra_ctx* c, const float* w, int64_t ld, int32_t on_device) {
+  if (!c) return CPRA_EINVAL;
+  if (!c->w_d) return fail(c, CPRA_EINVAL, "cpra_set_node_weights: not a weighted-MIS context");
+  if (!w || ld < c->S) return fail(c, CPRA_EINVAL, "cpra_set_node_weights: NULL or ld < S");
+  cudaStream_t st = c->stream;
+  c->have_eval = false;
+  cpra_status s = cuda_check(c, cudaMemsetAsync(c->w_d, 0, sizeof(float) * c->N * c->S_pad, st),
+                             "memset");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpy2DAsync(c->w_d, sizeof(float) * c->S_pad, w, sizeof(float) * ld,
+                                        sizeof(float) * c->S, c->N,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        st),
+                   "node weights");
+  if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+  return s;
 }
 
 cpra_status cpra_set_init_logits(cpra_ctx* c, const float* logits, int64_t ld, int32_t on_device) {

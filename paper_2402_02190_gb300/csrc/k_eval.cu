@@ -183,7 +183,40 @@ void launch_g(int64_t N, int S, int W, const int* rowptr, const int* col, const 
     eval_bits_kernel<G, 1><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
 }
 
+// Weighted MIS value per shot: block b sums w_is over its row range for the
+// shots set in the rounding bits, in row order; then the blocks in order.
+__global__ void weighted_value_kernel(int64_t N, int S, int W, const uint32_t* __restrict__ bits,
+                                      const float* __restrict__ w, int64_t ldw, int64_t rows_per,
+                                      double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+  const int64_t r1 = r0 + rows_per < N ? r0 + rows_per : N;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    double t = 0.0;
+    for (int64_t r = r0; r < r1; ++r)
+      if ((bits[r * W + (s >> 5)] >> (s & 31)) & 1u) t += (double)w[r * ldw + s];
+    part[(int64_t)blockIdx.x * S + s] = t;
+  }
+}
+
+__global__ void weighted_value_finalize(int blocks, int S, const double* __restrict__ part,
+                                        double* __restrict__ value) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double t = 0.0;
+  for (int b = 0; b < blocks; ++b) t += part[(int64_t)b * S + s];
+  value[s] = t;
+}
+
 }  // namespace
+
+void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* w, int64_t ldw,
+                           double* part, int max_blocks, double* value, cudaStream_t st) {
+  int64_t rows_per = (N + max_blocks - 1) / max_blocks;
+  if (rows_per < 1) rows_per = 1;
+  const int blocks = (int)((N + rows_per - 1) / rows_per);
+  weighted_value_kernel<<<blocks, 128, 0, st>>>(N, S, (S + 31) / 32, bits, w, ldw, rows_per, part);
+  weighted_value_finalize<<<(S + 127) / 128, 128, 0, st>>>(blocks, S, part, value);
+}
 
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
                       int problem, unsigned long long* counters, int max_grid, cudaStream_t st) {

@@ -122,13 +122,15 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
     const int ch = c * LPR + sub;
     if (ch >= nchG) continue;
     float out[4];
+    float wv[4] = {1.f, 1.f, 1.f, 1.f};  // weighted MIS: w_is of this chunk
+    if (PROBLEM == 0 && a.w) load16(a.w + i * a.ldw + ch * 4, wv);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int s = ch * 4 + e;
       const float pv = p[c][e], qv = q[c][e];
       float g;
       if (PROBLEM == 0) {
-        g = -1.f + lam[c][e] * qv;
+        g = -wv[e] + lam[c][e] * qv;
       } else {
         g = 2.f * qv - deg;
       }
@@ -144,7 +146,7 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
       if (a.grad_kind == 0) g *= pv * (1.f - pv);
       if (s < S) {
         if (PROBLEM == 0) {
-          acc.pc[c][e] -= pv;
+          acc.pc[c][e] -= wv[e] * pv;
           acc.pp[c][e] += 0.5f * pv * qv;
         } else {
           acc.pc[c][e] += pv * qv - deg * pv;
@@ -652,30 +654,34 @@ struct ShotEvalRec {
   long long objective;
   long long violations;
   double qubo;
+  double value;
 };
 
 __global__ void eval_finalize_kernel(const unsigned long long* __restrict__ cnt, int S,
                                      int problem, const float* __restrict__ lambda,
-                                     ShotEvalRec* out, long long* ham) {
+                                     const double* __restrict__ wvalue, ShotEvalRec* out,
+                                     long long* ham) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < S) {
     const long long obj = (long long)cnt[s];
     const long long viol = (long long)cnt[S + s];
+    const double value = wvalue ? wvalue[s] : (double)obj;
     double qubo;
-    if (problem == 0) qubo = -(double)obj + (double)lambda[s] * (double)viol;
-    else qubo = -(double)obj;
+    if (problem == 0) qubo = -value + (double)lambda[s] * (double)viol;
+    else qubo = -value;
     out[s].objective = obj;
     out[s].violations = (problem == 0) ? viol : 0;
     out[s].qubo = qubo;
+    out[s].value = value;
   }
   if (s == 0 && ham) *ham = (long long)cnt[2 * S];
 }
 
 void eval_finalize(const unsigned long long* counters, int S, int problem,
                    const float* lambda, void* out_records, long long* pair_hamming,
-                   cudaStream_t st) {
+                   cudaStream_t st, const double* wvalue) {
   eval_finalize_kernel<<<(S + 255) / 256, 256, 0, st>>>(
-      counters, S, problem, lambda, static_cast<ShotEvalRec*>(out_records), pair_hamming);
+      counters, S, problem, lambda, wvalue, static_cast<ShotEvalRec*>(out_records), pair_hamming);
 }
 
 }  // namespace cpra

@@ -132,8 +132,8 @@ namespace {
 // Single thread: the sums run in a fixed order with explicit roundings (no
 // contraction into fused multiply-adds), so the decision is reproducible.
 __global__ void early_stop_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
-                                  int S, float tol, int patience, const StepScalars* sc,
-                                  EarlyStopState* st) {
+                                  int S, float tol, int patience, float ann_below,
+                                  const StepScalars* sc, EarlyStopState* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0 || st->stopped) return;
   const float gamma = sc->gamma;
   const long long t = sc->t, updates = sc->updates;
@@ -145,7 +145,11 @@ __global__ void early_stop_kernel(const float* __restrict__ terms, const float* 
     ann = __dadd_rn(ann, (double)terms[2 * S + s]);
   }
   const double phi = __dmul_rn((double)gamma, ann);
-  if (st->have_prev) {
+  if (ann_below > 0.f && ann < (double)ann_below) {  // the annealing term has vanished
+    st->stopped = 1;
+    st->stop_step = t;
+    st->updates_at_stop = updates;
+  } else if (patience > 0 && st->have_prev) {
     const double dl = __dadd_rn(l, -st->prev_l), dp = __dadd_rn(phi, -st->prev_phi);
     const bool stale = (dl > 0.0 || fabs(dl) <= (double)tol) && (dp > 0.0 || fabs(dp) <= (double)tol);
     st->count = stale ? st->count + 1 : 0;
@@ -163,8 +167,9 @@ __global__ void early_stop_kernel(const float* __restrict__ terms, const float* 
 }  // namespace
 
 void early_stop_launch(const float* terms, const float* lambda, int S, float tol, int patience,
-                       const StepScalars* sc, EarlyStopState* st, cudaStream_t stream) {
-  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, tol, patience, sc, st);
+                       float ann_below, const StepScalars* sc, EarlyStopState* st,
+                       cudaStream_t stream) {
+  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, tol, patience, ann_below, sc, st);
 }
 
 namespace {
@@ -204,6 +209,19 @@ void step_scalars_launch(StepScalars* sc, int from_device, long long t, long lon
                          cudaStream_t st) {
   step_scalars_kernel<<<1, 32, 0, st>>>(sc, from_device, t, updates, gamma0, gamma1, T, beta1,
                                         beta2);
+}
+
+namespace {
+__global__ void fill_rows_kernel(int64_t N, int S, int64_t ld, float value, float* dst) {
+  const int64_t total = N * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (e % ld) < S ? value : 0.f;
+}
+}  // namespace
+
+void fill_rows_launch(int64_t N, int S, int64_t ld, float value, float* dst, cudaStream_t st) {
+  fill_rows_kernel<<<grid_for(N * ld), 256, 0, st>>>(N, S, ld, value, dst);
 }
 
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd, int ddst,

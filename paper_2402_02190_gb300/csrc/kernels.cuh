@@ -93,6 +93,8 @@ struct LossArgs {
   int problem = 0, alpha = 2, div_kind = 0, grad_kind = 0;
   float gamma = 0.f, nu = 0.f;
   const StepScalars* sc = nullptr;  // when set, gamma is sc->gamma
+  const float* w = nullptr;   // weighted MIS (problem 0): node weights N x ldw, cost -sum w P
+  int64_t ldw = 0;
   void* G = nullptr;             // dtype dg, N x ldg
   int dg = DT_F32;
   uint32_t* xbits = nullptr;     // N x W, W = ceil(S/32)
@@ -124,7 +126,12 @@ void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const
 // FP64 qubo value; pair-Hamming total copied out.
 void eval_finalize(const unsigned long long* counters, int S, int problem,
                    const float* lambda, void* out_records, long long* pair_hamming,
-                   cudaStream_t st);
+                   cudaStream_t st, const double* wvalue = nullptr);
+// Weighted MIS: value[s] = sum_i w_is x_is in FP64 from the rounding bits,
+// per-block partial rows (part[blocks][S], blocks <= max_blocks) summed in a
+// fixed order.
+void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* w, int64_t ldw,
+                           double* part, int max_blocks, double* value, cudaStream_t st);
 
 // ---------------------------------------------------------------- GEMM
 enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3,
@@ -200,9 +207,12 @@ struct EarlyStopState {
   int stopped;                // halts the parameter updates
   int pad;
 };
-// gamma, t and updates are the step's, read from sc.
+// gamma, t and updates are the step's, read from sc.  With ann_below > 0 a
+// step whose annealing sum falls below it also stops the run; patience 0
+// disables the stale-step rule.
 void early_stop_launch(const float* terms, const float* lambda, int S, float tol, int patience,
-                       const StepScalars* sc, EarlyStopState* st, cudaStream_t stream);
+                       float ann_below, const StepScalars* sc, EarlyStopState* st,
+                       cudaStream_t stream);
 // ---------------------------------------------------------------- warm start (k_warm.cu)
 // Node features [N x F]: 1, deg/8, then N(0,1) from the stream of `seed`.
 void ws_features_launch(int64_t N, const int* rowptr, uint64_t seed, int F, float* out,
@@ -222,6 +232,8 @@ int rows_colsum_launch(int64_t N, int C, const void* X, int64_t ldx, int dx, flo
 void weight_pair_launch(const float* W, int rows, int cols, int rows_pad, void* Ws, void* Wt,
                         cudaStream_t st);
 
+// dst[i*ld + k] = value for k < S, 0 for S <= k < ld.
+void fill_rows_launch(int64_t N, int S, int64_t ld, float value, float* dst, cudaStream_t st);
 void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd,
                       int ddst, cudaStream_t st);
 // BF16 shadows of the dense weights:

@@ -146,7 +146,7 @@ def test_op_round_eval_bit_exact(problem, S, N, gk):
     Pd[:, :S] = torch.from_numpy(P).cuda()
     W = (S + 31) // 32
     bits = torch.zeros((N, W), dtype=torch.int32, device="cuda")
-    rec = torch.zeros(S * 3, dtype=torch.float64, device="cuda")
+    rec = torch.zeros(S * 4, dtype=torch.float64, device="cuda")  # cpra_shot_eval [S]
     ham = torch.zeros(1, dtype=torch.int64, device="cuda")
     cnt = torch.empty(cpra.cpra_op_round_eval_scratch_bytes(S), dtype=torch.uint8, device="cuda")
     rpd, cold = dev_csr(rp, col)
@@ -172,7 +172,7 @@ def test_op_round_eval_threshold_edge_cases():
     for val, sel in ((0.5, 0), (np.nextafter(np.float32(0.5), np.float32(1)), 1)):
         Pd = torch.full((N, S), float(val), device="cuda")
         bits = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
-        rec = torch.zeros(S * 3, dtype=torch.float64, device="cuda")
+        rec = torch.zeros(S * 4, dtype=torch.float64, device="cuda")  # cpra_shot_eval [S]
         ham = torch.zeros(1, dtype=torch.int64, device="cuda")
         cnt = torch.empty(cpra.cpra_op_round_eval_scratch_bytes(S), dtype=torch.uint8, device="cuda")
         cpra.cpra_op_round_eval(rpd, cold, Pd, S, lam, O.MIS, bits, rec, ham, cnt)
