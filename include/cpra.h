@@ -199,6 +199,7 @@ CPRA_API cpra_status cpra_round_eval(cpra_ctx* ctx, cpra_shot_eval* out,
 /* Runs `steps` steps starting at schedule index 0 and, every eval_every
    steps and after the last, tracks per shot the best evaluation: MIS the
    largest objective with violations == 0 (objective -1 if none seen),
+   weighted MIS the largest value with violations == 0 (value -1 if none),
    MaxCut the largest cut.  best_out: host [S]; best_step_out: host [S] step
    index of that evaluation (or -1), may be NULL.  With es_patience > 0 the
    loop ends at the first evaluation after early stopping fired (the

@@ -1013,6 +1013,7 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
     best_out[s].objective = -1;
     best_out[s].violations = 0;
     best_out[s].qubo = 0.0;
+    best_out[s].value = -1.0;
   }
   for (int64_t t = 0; t < steps;) {
     // steps t .. t_eval in one call (a captured step replayed), then evaluate
@@ -1027,7 +1028,10 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
       if (st != CPRA_OK) return st;
       for (int s = 0; s < c->S; ++s) {
         const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
-        if (ok && cur[s].objective > best_out[s].objective) {
+        // weighted MIS ranks by total weight, the others by the integer objective
+        const bool better = c->wmis ? cur[s].value > best_out[s].value
+                                    : cur[s].objective > best_out[s].objective;
+        if (ok && better) {
           best_out[s] = cur[s];
           best_step[s] = t_eval;
         }
