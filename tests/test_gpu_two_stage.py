@@ -26,7 +26,7 @@ def test_two_stage_carries_and_freezes_the_encoder():
     assert r["encoder_unchanged"]
     assert r["feasible_tasks"] > S // 2
     ok = np.isfinite(r["best"])
-    assert np.all(r["best"][ok] > 0.0)
+    assert np.all(r["best"][ok] >= 0.0) and r["avg_weight"] > 0.0   # the empty set is feasible
     # a feasible weight never exceeds the sum of the task's weights
     assert np.all(r["best"][ok] <= W.sum(axis=0)[ok] + 1e-6)
     sc = TS.run_scratch(rp, col, W, lam, 1600, H=32, precision=cpra.BF16, eval_every=50, lr=1e-2)
