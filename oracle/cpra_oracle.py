@@ -54,6 +54,34 @@ import numpy as np
 MIS = 0
 MAXCUT = 1
 WMIS = 2   # weighted MIS (App. two-stage experiment): weight w_is of node i in task s
+DBM = 3    # diverse bipartite matching (Eq. matching-cost-function), one instance per shot
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def dbm_parts(P, inst):
+    """Row sums R (N1 x S), column sums K (N2 x S), totals T, U = sum M P and
+    the matching reward sum C P per shot, for variables x_ij at node i*N2 + j."""
+    N1, N2 = inst["N1"], inst["N2"]
+    S = P.shape[1]
+    X = P.reshape(N1, N2, S)
+    C = np.asarray(inst["C"], np.float64).reshape(N1, N2, S)
+    M = np.asarray(inst["M"], np.float64).reshape(N1, N2, S)
+    return dict(R=X.sum(axis=1), K=X.sum(axis=0), T=X.sum(axis=(0, 1)),
+                U=(M * X).sum(axis=(0, 1)), CP=(C * X).sum(axis=(0, 1)), C=C, M=M, X=X)
+
+
+def dbm_penalty(parts, inst):
+    """lambda-weighted penalty of Eq. matching-cost-function per shot."""
+    lam4 = np.asarray(inst["lam4"], np.float64)          # S x 4
+    pq = np.asarray(inst["pq"], np.float64)              # S x 2
+    T, U = parts["T"], parts["U"]
+    return (lam4[:, 0] * relu(parts["R"] - 1.0).sum(axis=0)
+            + lam4[:, 1] * relu(parts["K"] - 1.0).sum(axis=0)
+            + lam4[:, 2] * relu(pq[:, 0] * T - U)
+            + lam4[:, 3] * relu(pq[:, 1] * T - (T - U)))
 DIV_STD = 0
 DIV_VAR = 1
 
@@ -186,7 +214,7 @@ def shot_variance(P: np.ndarray) -> np.ndarray:
     return ((P - m[:, None]) ** 2).sum(axis=1) / S
 
 
-def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None):
+def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None, inst=None):
     """Per-shot cost_s, pen_s, ann_s and the shot-coupling Psi.
 
     MIS    l = -sum_i p_i + lambda sum_{(i,j) in E} p_i p_j
@@ -194,6 +222,9 @@ def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None)
     MaxCut l = sum_{i<j} A_ij (2 p_i p_j - p_i - p_j); cost_s = l, pen_s = 0
     WMIS   l = -sum_i w_i p_i + lambda sum_{(i,j) in E} p_i p_j (task s has its
            own node weights w_:s); cost_s = -sum_i w_is P_is, pen_s as MIS
+    DBM    Eq. matching-cost-function on x_ij = P_{i*N2+j}, instance (C, M,
+           lambda_1..4, p, q) of shot s in `inst`; cost_s = -sum C P and
+           pen_s = the four lambda-weighted ReLU terms (so l = cost + pen)
     ann_s  = sum_i 1 - (2 P_is - 1)^alpha
     Psi    = -S sum_i STD_s[P_is]        (STD form, Eq. ...-variation)
            = -S^2 sum_i VAR_s[P_is]      (VAR form, Prop. 3.2 left-hand side)
@@ -207,6 +238,10 @@ def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None)
     elif problem == WMIS:
         cost = -(np.asarray(weights, dtype=np.float64) * P).sum(axis=0)
         pen = (Pi * Pj).sum(axis=0)
+    elif problem == DBM:
+        parts = dbm_parts(P, inst)
+        cost = -parts["CP"]
+        pen = dbm_penalty(parts, inst)
     elif problem == MAXCUT:
         cost = (g.ew[:, None] * (2.0 * Pi * Pj - Pi - Pj)).sum(axis=0)
         pen = np.zeros(S)
@@ -226,12 +261,15 @@ def loss_terms(g: Graph, P, lam, problem, alpha, div_kind=DIV_STD, weights=None)
 def total_loss(terms, lam, gamma, nu, problem):
     lam = np.asarray(lam, dtype=np.float64)
     base = terms["cost"].sum()
-    if problem in (MIS, WMIS):
+    if problem == DBM:
+        base += terms["pen"].sum()            # already lambda-weighted
+    elif problem in (MIS, WMIS):
         base += (lam * terms["pen"]).sum()
     return base + gamma * terms["ann"].sum() + nu * terms["psi"]
 
 
-def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD, weights=None):
+def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD, weights=None,
+           inst=None):
     """dR/dP_is, analytic, with the edge list traversed once per edge."""
     P = np.asarray(P, dtype=np.float64)
     N, S = P.shape
@@ -241,6 +279,21 @@ def grad_P(g: Graph, P, lam, problem, alpha, gamma, nu, div_kind=DIV_STD, weight
         G -= 1.0 if problem == MIS else np.asarray(weights, dtype=np.float64)
         np.add.at(G, g.ei, lam[None, :] * P[g.ej])
         np.add.at(G, g.ej, lam[None, :] * P[g.ei])
+    elif problem == DBM:
+        # d/dx_ij of Eq. matching-cost-function, ReLU'(0) = 0
+        parts = dbm_parts(P, inst)
+        lam4 = np.asarray(inst["lam4"], np.float64)
+        pq = np.asarray(inst["pq"], np.float64)
+        T, U = parts["T"], parts["U"]
+        N1, N2 = inst["N1"], inst["N2"]
+        rows = (parts["R"] > 1.0).astype(np.float64)        # N1 x S
+        cols = (parts["K"] > 1.0).astype(np.float64)        # N2 x S
+        on3 = (pq[:, 0] * T - U > 0.0).astype(np.float64)
+        on4 = (pq[:, 1] * T - (T - U) > 0.0).astype(np.float64)
+        Gd = (-parts["C"] + lam4[:, 0] * rows[:, None, :] + lam4[:, 1] * cols[None, :, :]
+              + lam4[:, 2] * on3 * (pq[:, 0] - parts["M"])
+              + lam4[:, 3] * on4 * (pq[:, 1] - (1.0 - parts["M"])))
+        G += Gd.reshape(N1 * N2, S)
     else:
         w = g.ew[:, None]
         np.add.at(G, g.ei, w * (2.0 * P[g.ej] - 1.0))
@@ -313,7 +366,7 @@ def gamma_schedule(t, T, gamma0, gamma1):
 def early_stop_step(terms_seq, gammas, lam, problem, tol, patience, ann_below=0.0):
     """Early stopping of the Implementation paragraph: the run is monitored
     through the summed penalty-form loss l_t = sum_s (cost_s + lambda_s pen_s)
-    (MaxCut: sum_s cost_s) and the annealing term phi_t = gamma_t sum_s ann_s,
+    (MaxCut: sum_s cost_s; DBM: sum_s (cost_s + pen_s)) and the annealing term phi_t = gamma_t sum_s ann_s,
     with a tolerance and a patience.  Reading (the paper gives only the two
     numbers): step t > 0 is stale when, for both monitored values, the change
     from step t-1 is positive or at most `tol` in magnitude; the run stops at
@@ -335,6 +388,8 @@ def early_stop_step(terms_seq, gammas, lam, problem, tol, patience, ann_below=0.
             ls = float(cost[s])
             if problem in (MIS, WMIS):
                 ls = ls + float(lam[s]) * float(pen[s])
+            elif problem == DBM:
+                ls = ls + float(pen[s])          # the DBM penalty carries its own lambdas
             l_t = l_t + ls
             a_t = a_t + float(ann[s])
         phi_t = float(gamma) * a_t
@@ -359,16 +414,27 @@ def round_solutions(P) -> np.ndarray:
     return (np.asarray(P) > 0.5).astype(np.int64)
 
 
-def integer_eval(g: Graph, X, lam, problem, weights=None):
+def integer_eval(g: Graph, X, lam, problem, weights=None, inst=None):
     """Per shot: objective (MIS set size / MaxCut cut size), violations
     (MIS: edges with both ends selected; MaxCut: 0), qubo value l(x), the
     objective in the problem's own units `value` (set size, total weight of
     the set for weighted MIS, cut size), and the pairwise Hamming sum
-    sum_{s<l} d_H(x_s, x_l)."""
+    sum_{s<l} d_H(x_s, x_l).  DBM: objective = matched pairs sum x, violations =
+    rows and columns with more than one pair plus the two diversity
+    constraints that fail, value = sum C x, qubo = l(x)."""
     X = np.asarray(X, dtype=np.int64)
     N, S = X.shape
     Xi, Xj = X[g.ei], X[g.ej]
-    if problem in (MIS, WMIS):
+    if problem == DBM:
+        parts = dbm_parts(X.astype(np.float64), inst)
+        pq = np.asarray(inst["pq"], np.float64)
+        T, U = parts["T"], parts["U"]
+        obj = X.sum(axis=0)
+        viol = ((parts["R"] > 1.0).sum(axis=0) + (parts["K"] > 1.0).sum(axis=0)
+                + (pq[:, 0] * T - U > 0.0) + (pq[:, 1] * T - (T - U) > 0.0))
+        value = parts["CP"]
+        qubo = -value + dbm_penalty(parts, inst)
+    elif problem in (MIS, WMIS):
         obj = X.sum(axis=0)
         viol = (Xi * Xj).sum(axis=0)
         value = obj.astype(np.float64)
@@ -414,10 +480,11 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
     cache = forward(g, theta, X0, H0, H1, S, cfg.get("relu_decision"), cfg.get("init_logits"))
     P = cache["P"]
     W = cfg.get("weights")
-    terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"], W)
+    inst = cfg.get("dbm")
+    terms = loss_terms(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["div_kind"], W, inst)
     L = total_loss(terms, cfg["lam"], cfg["gamma"], cfg["nu"], cfg["problem"])
     G_P = grad_P(g, P, cfg["lam"], cfg["problem"], cfg["alpha"], cfg["gamma"],
-                 cfg["nu"], cfg["div_kind"], W)
+                 cfg["nu"], cfg["div_kind"], W, inst)
     grads = backward(g, theta, cache, G_P, H0, H1, S)
     if adam_state is None:
         adam_state = dict(m_theta=np.zeros(len(theta)), v_theta=np.zeros(len(theta)),
@@ -439,7 +506,7 @@ def step(g: Graph, theta, X0, cfg, t, adam_state=None):
         mx = np.asarray(adam_state["m_X0"], np.float64)
         vx = np.asarray(adam_state["v_X0"], np.float64)
     X = round_solutions(P)
-    ev = integer_eval(g, X, cfg["lam"], cfg["problem"], W)
+    ev = integer_eval(g, X, cfg["lam"], cfg["problem"], W, inst)
     return dict(cache=cache, P=P, terms=terms, loss=L, G_P=G_P, grads=grads,
                 theta_next=th1, X0_next=x1,
                 adam_next=dict(m_theta=mt, v_theta=vt, m_X0=mx, v_X0=vx),

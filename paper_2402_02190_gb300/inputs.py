@@ -266,3 +266,39 @@ def unpack_bits(bits, S: int) -> np.ndarray:
     for s in range(S):
         out[:, s] = (bits[:, s // 32] >> np.uint32(s % 32)) & np.uint32(1)
     return out
+
+
+# ------------------------------------------------------------ diverse bipartite matching
+def dbm_graph(N1: int, N2: int):
+    """GNN graph of an N1 x N2 matching problem: the node of x_ij (index
+    i*N2 + j) is adjacent to every x_ik (same row) and x_kj (same column), the
+    variables that share one of its constraints.  Symmetric CSR, sorted rows."""
+    rows = []
+    for i in range(N1):
+        for j in range(N2):
+            nb = [i * N2 + k for k in range(N2) if k != j] + [k * N2 + j for k in range(N1) if k != i]
+            rows.append(sorted(nb))
+    rowptr = np.zeros(N1 * N2 + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([v for r in rows for v in r], dtype=np.int32)
+    return rowptr, col
+
+
+def dbm_instance(N1: int, N2: int, seed: int, n_fields: int = 7, p: float = 0.25, q: float = 0.25):
+    """Seeded stand-in for one CORA-derived matching instance: rewards C_ij
+    (link likelihoods, skewed towards 0) and M_ij = 1 when the two papers'
+    fields differ (fields drawn uniformly), flattened to node order i*N2 + j.
+    Returns (C [N], M [N], p, q)."""
+    rng = np.random.default_rng(seed)
+    C = rng.random((N1, N2)) ** 3
+    f1 = rng.integers(0, n_fields, size=N1)
+    f2 = rng.integers(0, n_fields, size=N2)
+    M = (f1[:, None] != f2[None, :]).astype(np.float64)
+    return C.ravel().astype(np.float32), M.ravel().astype(np.float32), p, q
+
+
+def dbm_lambda_grid(n: int = 11):
+    """The penalty grid of the DBM experiment: lambda_s = (a, a, b, b) with
+    a, b in {2^0, ..., 2^(n-1)}; returns [n*n, 4]."""
+    v = 2.0 ** np.arange(n)
+    return np.array([(a, a, b, b) for a in v for b in v], dtype=np.float32)

@@ -1,0 +1,121 @@
+"""Pins of the oracle's diverse bipartite matching loss (Eq.
+matching-cost-function): direct formula at binary points, brute-force
+optimum, finite differences, violation counts, and the constraint graph."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import cpra_oracle as O
+from paper_2402_02190_gb300 import inputs as I
+
+
+def _inst(N1, N2, S, seed, p=0.25, q=0.25):
+    rng = np.random.default_rng(seed)
+    C = rng.random((N1 * N2, S))
+    M = (rng.random((N1 * N2, S)) < 0.5).astype(np.float64)
+    lam4 = rng.uniform(0.5, 4.0, size=(S, 4))
+    pq = np.tile([p, q], (S, 1))
+    return dict(N1=N1, N2=N2, C=C, M=M, lam4=lam4, pq=pq)
+
+
+def _direct(x, C, M, lam, p, q, N1, N2):
+    """l(x) of Eq. matching-cost-function written with explicit loops."""
+    r = lambda v: v if v > 0 else 0.0
+    X = [[x[i * N2 + j] for j in range(N2)] for i in range(N1)]
+    val = -sum(C[i * N2 + j] * X[i][j] for i in range(N1) for j in range(N2))
+    val += lam[0] * sum(r(sum(X[i]) - 1) for i in range(N1))
+    val += lam[1] * sum(r(sum(X[i][j] for i in range(N1)) - 1) for j in range(N2))
+    T = sum(sum(row) for row in X)
+    U = sum(M[i * N2 + j] * X[i][j] for i in range(N1) for j in range(N2))
+    val += lam[2] * r(p * T - U) + lam[3] * r(q * T - (T - U))
+    return val
+
+
+def _graph(N1, N2):
+    rp, col = I.dbm_graph(N1, N2)
+    return O.Graph(rp, col)
+
+
+@pytest.mark.parametrize("N1,N2", [(2, 3), (3, 3)])
+def test_relaxation_equals_direct_formula_at_binary_points(N1, N2):
+    N = N1 * N2
+    xs = np.array(list(itertools.product([0, 1], repeat=N)), dtype=np.float64).T   # N x 2^N
+    S = xs.shape[1]
+    inst = _inst(N1, N2, S, seed=N)
+    g = _graph(N1, N2)
+    t = O.loss_terms(g, xs, np.ones(S), O.DBM, 2, inst=inst)
+    assert np.all(t["ann"] == 0.0)
+    for s in range(0, S, 5):
+        want = _direct(xs[:, s], inst["C"][:, s], inst["M"][:, s], inst["lam4"][s], 0.25, 0.25, N1, N2)
+        assert t["cost"][s] + t["pen"][s] == pytest.approx(want, abs=1e-12)
+    ev = O.integer_eval(g, xs.astype(np.int64), np.ones(S), O.DBM, inst=inst)
+    assert np.allclose(ev["qubo"], t["cost"] + t["pen"], rtol=0, atol=1e-12)
+
+
+def test_large_penalties_give_the_best_diverse_matching():
+    """With large lambdas the QUBO minimum is minus the heaviest matching that
+    meets both diversity constraints, found by enumerating matchings."""
+    N1, N2 = 3, 3
+    rng = np.random.default_rng(4)
+    C = rng.random(N1 * N2)
+    M = np.array([0, 1, 1, 1, 0, 1, 1, 1, 0], dtype=np.float64)
+    p, q = 0.25, 0.25
+    best = 0.0
+    for xbits in itertools.product([0, 1], repeat=9):
+        X = np.array(xbits).reshape(3, 3)
+        if (X.sum(axis=1) > 1).any() or (X.sum(axis=0) > 1).any():
+            continue
+        T, U = X.sum(), (M.reshape(3, 3) * X).sum()
+        if p * T - U > 0 or q * T - (T - U) > 0:
+            continue
+        best = max(best, float((C.reshape(3, 3) * X).sum()))
+    xs = np.array(list(itertools.product([0, 1], repeat=9)), dtype=np.float64).T
+    S = xs.shape[1]
+    inst = dict(N1=3, N2=3, C=np.repeat(C[:, None], S, 1), M=np.repeat(M[:, None], S, 1),
+                lam4=np.full((S, 4), 50.0), pq=np.tile([p, q], (S, 1)))
+    t = O.loss_terms(_graph(3, 3), xs, np.ones(S), O.DBM, 2, inst=inst)
+    assert (t["cost"] + t["pen"]).min() == pytest.approx(-best, abs=1e-12)
+
+
+def test_gradient_matches_finite_differences():
+    N1, N2, S = 3, 4, 5
+    inst = _inst(N1, N2, S, seed=9)
+    g = _graph(N1, N2)
+    rng = np.random.default_rng(1)
+    P = rng.uniform(0.05, 0.95, size=(N1 * N2, S))
+
+    def R(Pm):
+        t = O.loss_terms(g, Pm, np.ones(S), O.DBM, 4, O.DIV_STD, inst=inst)
+        return O.total_loss(t, np.ones(S), 0.6, 0.3, O.DBM)
+
+    G = O.grad_P(g, P, np.ones(S), O.DBM, 4, 0.6, 0.3, O.DIV_STD, inst=inst)
+    h = 1e-7
+    fd = np.zeros_like(P)
+    for idx in np.ndindex(*P.shape):
+        a = P.copy(); a[idx] += h
+        b = P.copy(); b[idx] -= h
+        fd[idx] = (R(a) - R(b)) / (2 * h)
+    # no ReLU kink lies within h of this P
+    parts = O.dbm_parts(P, inst)
+    assert np.abs(parts["R"] - 1).min() > 1e-4 and np.abs(parts["K"] - 1).min() > 1e-4
+    assert np.linalg.norm(G - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_violation_counts():
+    N1, N2 = 2, 3
+    inst = dict(N1=2, N2=3, C=np.ones((6, 1)), M=np.array([[0], [1], [1], [1], [0], [1]], float),
+                lam4=np.ones((1, 4)), pq=np.array([[0.6, 0.5]]))
+    x = np.array([[1], [1], [0], [0], [1], [0]])     # row 0 has two pairs, column 1 two pairs
+    ev = O.integer_eval(_graph(2, 3), x, np.ones(1), O.DBM, inst=inst)
+    # T = 3, U = M.x = 1: p T - U = 0.8 > 0 (violated), q T - (T - U) = -0.5 (met)
+    assert ev["objective"][0] == 3 and ev["violations"][0] == 1 + 1 + 1
+    assert ev["value"][0] == 3.0
+
+
+def test_constraint_graph():
+    rp, col = I.dbm_graph(4, 5)
+    assert np.all(np.diff(rp) == 4 + 5 - 2)
+    edges = set(zip(np.repeat(np.arange(20), np.diff(rp)).tolist(), col.tolist()))
+    assert all((j, i) in edges for i, j in edges)
+    assert (0 * 5 + 1, 0) in edges and (1 * 5 + 0, 0) in edges and (1 * 5 + 1, 0) not in edges
