@@ -55,15 +55,18 @@ typedef enum {
 } cpra_status;
 
 enum { CPRA_MIS = 0, CPRA_MAXCUT = 1,                 /* Table objective-functions */
-       CPRA_WMIS = 2 };  /* weighted MIS: shot s solves the MIS QUBO with node weights
+       CPRA_WMIS = 2,    /* weighted MIS: shot s solves the MIS QUBO with node weights
                             w_:s (the task family of the paper's two-stage experiment);
                             weights from cpra_set_node_weights, 1 until set */
+       CPRA_DBM = 3 };   /* diverse bipartite matching (Eq. matching-cost-function):
+                            node i*N2 + j is the pair variable x_ij; shot s has its
+                            own instance (C, M, lambda_1..4, p, q) from cpra_set_dbm */
 enum { CPRA_FP32 = 0, CPRA_BF16 = 1 };                /* dense-layer arithmetic   */
 enum { CPRA_DIV_STD = 0, CPRA_DIV_VAR = 1 };          /* Psi form                 */
 
 /* Configuration.  cpra_config_default() fills every field. */
 typedef struct cpra_config {
-  int32_t problem;          /* CPRA_MIS or CPRA_MAXCUT                           */
+  int32_t problem;          /* CPRA_MIS, CPRA_MAXCUT, CPRA_WMIS or CPRA_DBM       */
   int32_t S;                /* shots = columns of P, 1..1024                      */
   int32_t H0;               /* node-embedding width (multiple of 16, <= 1024)    */
   int32_t H1;               /* hidden width (multiple of 16, <= 1024)            */
@@ -81,8 +84,9 @@ typedef struct cpra_config {
                                not store dR/dh^0; 1: it also stores dR/dh^0
                                (CPRA_T_EMB_GRAD), 512 MB more HBM traffic per
                                10^6 x 128 embedding                             */
-  const float* lambda;      /* host [S], penalty lambda_s per shot (MIS); copied
-                               at init; may be NULL for MaxCut                     */
+  const float* lambda;      /* host [S], penalty lambda_s per shot ((W)MIS);
+                               copied at init; may be NULL for MaxCut and DBM (not
+                               read: DBM penalties come with cpra_set_dbm)         */
   float nu;                 /* diversity weight (0 disables Psi)                  */
   float gamma0, gamma1;     /* annealing: gamma_t linear from gamma0 to gamma1    */
   int64_t schedule_steps;   /*   over t = 0 .. schedule_steps-1                   */
@@ -112,12 +116,16 @@ typedef struct cpra_config {
 
 /* Result of rounding one shot (App. C.2) and evaluating it exactly. */
 typedef struct cpra_shot_eval {
-  int64_t objective;   /* (W)MIS: |{i : x_i = 1}|;  MaxCut: number of cut edges */
-  int64_t violations;  /* (W)MIS: edges with both ends in the set; MaxCut: 0     */
+  int64_t objective;   /* (W)MIS: |{i : x_i = 1}|;  MaxCut: number of cut edges;
+                          DBM: matched pairs sum_ij x_ij                       */
+  int64_t violations;  /* (W)MIS: edges with both ends in the set; MaxCut: 0;
+                          DBM: rows and columns with more than one pair plus the
+                          diversity constraints (of 2) that fail               */
   double qubo;         /* l(x): -value + lambda_s * violations ((W)MIS);
-                          -value (MaxCut)                                       */
+                          -value (MaxCut); Eq. matching-cost-function (DBM), FP64 */
   double value;        /* objective in the problem's units: set size, total
-                          weight sum_i w_is x_is (WMIS, FP64), cut size      */
+                          weight sum_i w_is x_is (WMIS, FP64), cut size,
+                          reward sum_ij C_ij x_ij (DBM, FP64)                  */
 } cpra_shot_eval;
 
 typedef struct cpra_ctx cpra_ctx;
@@ -213,6 +221,28 @@ CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every
    Synchronises.  Errors: CPRA_EINVAL (not a WMIS context, NULL, ld < S). */
 CPRA_API cpra_status cpra_set_node_weights(cpra_ctx* ctx, const float* w, int64_t ld,
                                            int32_t on_device);
+
+/* Diverse bipartite matching instances (problem CPRA_DBM; Eq.
+   matching-cost-function, App. problem specification).  The graph given to
+   cpra_init_graph has N = N1 * N2 nodes, node i*N2 + j being the pair
+   variable x_ij (i < N1 on one side, j < N2 on the other).  Shot s carries
+   its own instance: C and M are float [N x ld] (ld >= S, row-major),
+   C[(i*N2+j)*ld + s] the reward C_ij of shot s and M[...] its field
+   indicator (1: i and j are in different fields, 0: the same field; any
+   value in [0, 1] is accepted); lam4 is float [S x 4], the penalties
+   (lambda_1, lambda_2, lambda_3, lambda_4) of shot s, and pq float [S x 2]
+   its diversity shares (p, q).  All on the host.  The penalty grid (one
+   instance repeated, S penalty vectors) and multi-instance CPRA (S
+   instances, one penalty vector; App. multi-instance) are both this layout.
+   The library copies them into device memory it allocates itself (2 N
+   round_up(S,16) floats plus line buffers of about 6 (N1 + N2) round_up(S,16)
+   floats, counted against mem_cap_bytes, freed by cpra_destroy).  Required
+   before the first step, forward or evaluation of a DBM context; a later call
+   with the same N1 replaces the instances in place.  Synchronises.  Errors:
+   CPRA_EINVAL (not a DBM context, a NULL array, ld < S, N1 < 1 or not dividing
+   N, a non-finite value, p or q or M outside [0, 1]), CPRA_ENOMEM. */
+CPRA_API cpra_status cpra_set_dbm(cpra_ctx* ctx, int32_t N1, const float* C, const float* M,
+                                  int64_t ld, const float* lam4, const float* pq);
 
 /* Schedule index t of the cpra_step at which early stopping fired, or -1
    (also when es_patience is 0).  Synchronises. */

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libcpra.so")
 
 CPRA_OK, CPRA_EINVAL, CPRA_ENOMEM, CPRA_ECUDA, CPRA_ENUMERIC, CPRA_ETIMEOUT, CPRA_ESTATE = range(7)
-MIS, MAXCUT, WMIS = 0, 1, 2
+MIS, MAXCUT, WMIS, DBM = 0, 1, 2, 3
 FP32, BF16 = 0, 1
 DIV_STD, DIV_VAR = 0, 1
 (T_THETA, T_THETA_M, T_THETA_V, T_EMB, T_EMB_M, T_EMB_V, T_GRAD, T_EMB_GRAD, T_P, T_GZ2,
@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
     "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
-    "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
+    "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_set_dbm", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
     "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
     "cpra_ws_set_params", "cpra_ws_destroy",
 )
@@ -112,6 +112,7 @@ def lib():
         "cpra_early_stop_step": (i64, [vp]),
         "cpra_steps": (i32, [vp, i64, i64]),
         "cpra_set_node_weights": (i32, [vp, vp, i64, i32]),
+        "cpra_set_dbm": (i32, [vp, i32, vp, vp, i64, vp, vp]),
         "cpra_set_init_logits": (i32, [vp, vp, i64, i32]),
         "cpra_profile_enable": (None, [vp, C.c_int]),
         "cpra_profile_read": (i32, [vp, vp, vp, i32]),
@@ -320,6 +321,18 @@ def cpra_set_node_weights(ctx, w) -> None:
     _check(lib().cpra_set_node_weights(ctx, _ptr(a), a.shape[1], 0), ctx)
 
 
+def cpra_set_dbm(ctx, N1: int, C_rew, M, lam4, pq) -> None:
+    """Matching instances of a DBM context: C_rew, M host arrays [N, S]
+    (node i*N2 + j, shot s), lam4 [S, 4] = (lambda_1..4), pq [S, 2] = (p, q)."""
+    c = np.ascontiguousarray(C_rew, dtype=np.float32)
+    m = np.ascontiguousarray(M, dtype=np.float32)
+    l4 = np.ascontiguousarray(lam4, dtype=np.float32)
+    pqa = np.ascontiguousarray(pq, dtype=np.float32)
+    if c.shape != m.shape or c.ndim != 2 or l4.shape != (c.shape[1], 4) or pqa.shape != (c.shape[1], 2):
+        raise ValueError("cpra_set_dbm: C, M [N, S], lam4 [S, 4], pq [S, 2]")
+    _check(lib().cpra_set_dbm(ctx, int(N1), _ptr(c), _ptr(m), c.shape[1], _ptr(l4), _ptr(pqa)), ctx)
+
+
 def cpra_steps(ctx, t0: int, n: int) -> None:
     _check(lib().cpra_steps(ctx, int(t0), int(n)), ctx)
 
@@ -454,6 +467,9 @@ class Solver:
             import torch
             self.stream.wait_stream(torch.cuda.current_stream())
         cpra_set_node_weights(self.ctx, w)
+
+    def set_dbm(self, N1: int, C_rew, M, lam4, pq) -> None:
+        cpra_set_dbm(self.ctx, N1, C_rew, M, lam4, pq)
 
     def steps(self, t0: int, n: int) -> None:
         cpra_steps(self.ctx, t0, n)

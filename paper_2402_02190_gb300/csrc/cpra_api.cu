@@ -44,6 +44,7 @@ enum KernelId {
   K_ADAM_EMB,
   K_EVAL,
   K_RECOMPUTE_MASK,
+  K_DBM_SUMS,
   K_COUNT_
 };
 
@@ -51,7 +52,7 @@ const char* kKernelNames[K_COUNT_] = {
     "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
     "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
     "gemm_dgrad1", "spmm_bwd1",   "adam",       "spmm_bwd1_adam_embedding", "round_eval",
-    "recompute_layer1_mask"};
+    "recompute_layer1_mask", "dbm_line_sums"};
 
 constexpr size_t kAlign = 256;
 constexpr int kWvBlocks = 512;  // weighted-MIS value partial rows
@@ -124,6 +125,9 @@ struct cpra_ctx {
   double* wv_part = nullptr;      // weighted MIS: per-block value partials
   double* wvalue = nullptr;       // weighted MIS: per-shot value
   bool wmis = false;
+  DbmDev dbm;                     // matching instances (problem DBM)
+  void* dbm_mem = nullptr;        // own cudaMalloc behind dbm, null until cpra_set_dbm
+  int64_t dbm_bytes = 0;
   void* init_logits = nullptr;    // warm start: N x S_pad act dtype, own cudaMalloc
   StepScalars* sc = nullptr;      // per-step gamma / bias corrections (device)
   // one captured training step, replayed by cpra_steps / cpra_solve
@@ -191,8 +195,9 @@ Layout layout_of(int H0, int H1, int S) {
 
 std::string validate_config(const cpra_config* cfg) {
   if (!cfg) return "cfg is NULL";
-  if (cfg->problem != CPRA_MIS && cfg->problem != CPRA_MAXCUT && cfg->problem != CPRA_WMIS)
-    return "problem must be MIS, MAXCUT or WMIS";
+  if (cfg->problem != CPRA_MIS && cfg->problem != CPRA_MAXCUT && cfg->problem != CPRA_WMIS &&
+      cfg->problem != CPRA_DBM)
+    return "problem must be MIS, MAXCUT, WMIS or DBM";
   if (cfg->S < 1 || cfg->S > 1024) return "S must be in [1, 1024]";
   if (cfg->H0 < 16 || cfg->H0 > 1024 || cfg->H0 % 16) return "H0 must be a multiple of 16 in [16, 1024]";
   if (cfg->H1 < 16 || cfg->H1 > 1024 || cfg->H1 % 16) return "H1 must be a multiple of 16 in [16, 1024]";
@@ -203,7 +208,8 @@ std::string validate_config(const cpra_config* cfg) {
   if (cfg->recompute != 0 && cfg->recompute != 1) return "recompute must be 0 or 1";
   if (cfg->es_patience < 0 || !(cfg->es_tol >= 0.f) || !std::isfinite(cfg->es_tol))
     return "early stopping needs es_patience >= 0 and a finite es_tol >= 0";
-  if (cfg->problem != CPRA_MAXCUT && cfg->lambda == nullptr) return "MIS needs lambda[S]";
+  if ((cfg->problem == CPRA_MIS || cfg->problem == CPRA_WMIS) && cfg->lambda == nullptr)
+    return "MIS needs lambda[S]";
   if (cfg->train_encoder != 0 && cfg->train_encoder != 1) return "train_encoder must be 0 or 1";
   if (!(cfg->es_ann_below >= 0.f) || !std::isfinite(cfg->es_ann_below))
     return "es_ann_below must be finite and >= 0";
@@ -441,6 +447,8 @@ void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_
 
 cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
                                  const StepScalars* sc = nullptr) {
+  const bool dbm = c->cfg.problem == CPRA_DBM;
+  if (dbm && !c->dbm_mem) return fail(c, CPRA_ESTATE, "DBM context: call cpra_set_dbm first");
   const int64_t N = c->N;
   const int H0 = c->H0, H1 = c->H1;
   const int max_grid = c->num_sms * 8;
@@ -488,13 +496,20 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     if (c->init_logits) { g.addend = c->init_logits; g.ld_add = c->S_pad; g.d_add = c->act_dt; }
     dense(c, g);
   }
+  if (dbm && do_loss) {  // matching line sums R, K, T, U and the per-shot coefficients
+    Region r(c, K_DBM_SUMS);
+    dbm_sums_launch(c->dbm, c->S, c->P, c->S_pad, c->stream);
+    c->launches += 2;
+  }
   int grid = 0;
   {  // fused SpMM + loss + rounding bits
     Region r(c, K_LOSS);
     LossArgs a;
     a.N = N; a.S = c->S; a.ldp = c->S_pad; a.ldg = c->S_pad;
     a.rowptr = c->rowptr; a.col = c->col; a.P = c->P; a.lambda = c->lambda_d;
-    a.problem = c->cfg.problem == CPRA_MAXCUT ? 1 : 0;  // weighted MIS: MIS with weights
+    // weighted MIS: MIS with weights
+    a.problem = dbm ? 2 : c->cfg.problem == CPRA_MAXCUT ? 1 : 0;
+    a.dbm = c->dbm;
     a.w = c->w_d; a.ldw = c->S_pad;
     a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
     a.grad_kind = 0; a.gamma = gamma; a.sc = do_loss ? sc : nullptr; a.nu = c->cfg.nu;
@@ -522,9 +537,15 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
                             c->wvalue, c->stream);
       c->launches += 2;
     }
-    eval_finalize(c->counters, c->S, c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->lambda_d,
-                  c->eval_rec, c->ham_d, c->stream, c->w_d ? c->wvalue : nullptr);
-    c->launches += 2;
+    if (dbm) {  // matchings: line counts, constraints and rewards (the set size and
+                // pair-Hamming counters above are problem-independent)
+      dbm_eval_launch(c->dbm, c->S, c->xbits, c->counters, c->eval_rec, c->ham_d, c->stream);
+      c->launches += 3;
+    } else {
+      eval_finalize(c->counters, c->S, c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->lambda_d,
+                    c->eval_rec, c->ham_d, c->stream, c->w_d ? c->wvalue : nullptr);
+      c->launches += 2;
+    }
   }
   c->have_eval = true;
   return CPRA_OK;
@@ -746,7 +767,10 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   c->num_sms = device_sm_count();
   set_dims(c, N, rowptr[N], cfg);
   c->lambda_h.assign((size_t)c->S, 0.f);
-  if (cfg->lambda) std::memcpy(c->lambda_h.data(), cfg->lambda, sizeof(float) * c->S);
+  if (cfg->problem == CPRA_DBM)  // the matching penalty carries its own lambdas
+    c->lambda_h.assign((size_t)c->S, 1.f);
+  else if (cfg->lambda)
+    std::memcpy(c->lambda_h.data(), cfg->lambda, sizeof(float) * c->S);
   c->cfg.lambda = nullptr;
   c->use_tc = (c->act_dt == DT_BF16) && tc_available();
 
@@ -1028,9 +1052,12 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
       if (st != CPRA_OK) return st;
       for (int s = 0; s < c->S; ++s) {
         const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
-        // weighted MIS ranks by total weight, the others by the integer objective
-        const bool better = c->wmis ? cur[s].value > best_out[s].value
-                                    : cur[s].objective > best_out[s].objective;
+        // weighted MIS and DBM rank by value (weight, reward), the others by
+        // the integer objective; objective -1 marks a shot with none yet
+        const bool by_value = c->wmis || c->cfg.problem == CPRA_DBM;
+        const bool better = best_out[s].objective < 0 ||
+                            (by_value ? cur[s].value > best_out[s].value
+                                      : cur[s].objective > best_out[s].objective);
         if (ok && better) {
           best_out[s] = cur[s];
           best_step[s] = t_eval;
@@ -1299,6 +1326,7 @@ void cpra_destroy(cpra_ctx* c) {
     if (r.b) cudaEventDestroy(r.b);
   }
   drop_graph(c);
+  if (c->dbm_mem) cudaFree(c->dbm_mem);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1319,6 +1347,94 @@ cpra_status cpra_set_node_weights(cpra_ctx* c, const float* w, int64_t ld, int32
                                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                         st),
                    "node weights");
+  if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "sync");
+  return s;
+}
+
+cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M, int64_t ld,
+                         const float* lam4, const float* pq) {
+  if (!c) return CPRA_EINVAL;
+  if (c->cfg.problem != CPRA_DBM) return fail(c, CPRA_EINVAL, "cpra_set_dbm: not a DBM context");
+  if (!C || !M || !lam4 || !pq) return fail(c, CPRA_EINVAL, "cpra_set_dbm: NULL array");
+  if (ld < c->S) return fail(c, CPRA_EINVAL, "cpra_set_dbm: ld < S");
+  if (N1 < 1 || c->N % N1) return fail(c, CPRA_EINVAL, "cpra_set_dbm: N1 must divide N");
+  const int S = c->S;
+  for (int64_t n = 0; n < c->N; ++n)
+    for (int s = 0; s < S; ++s) {
+      const float cv = C[n * ld + s], mv = M[n * ld + s];
+      if (!std::isfinite(cv)) return fail(c, CPRA_EINVAL, "cpra_set_dbm: non-finite C");
+      if (!(mv >= 0.f && mv <= 1.f)) return fail(c, CPRA_EINVAL, "cpra_set_dbm: M outside [0, 1]");
+    }
+  for (int s = 0; s < S; ++s) {
+    for (int k = 0; k < 4; ++k)
+      if (!std::isfinite(lam4[4 * s + k])) return fail(c, CPRA_EINVAL, "cpra_set_dbm: non-finite lambda");
+    for (int k = 0; k < 2; ++k)
+      if (!(pq[2 * s + k] >= 0.f && pq[2 * s + k] <= 1.f))
+        return fail(c, CPRA_EINVAL, "cpra_set_dbm: p, q outside [0, 1]");
+  }
+  const int N2 = (int)(c->N / N1);
+  const int64_t ldd = c->S_pad;
+  const int lines = N1 + N2;
+  // one allocation: C, M, rowc, colc, line sums, shot coefficients, eval partials
+  auto carve_dbm = [&](void* base, DbmDev& d) -> size_t {
+    Carver cv(base);
+    float* Cd = cv.take<float>((size_t)c->N * ldd);
+    float* Md = cv.take<float>((size_t)c->N * ldd);
+    float* l4 = cv.take<float>((size_t)4 * S);
+    float* pqd = cv.take<float>((size_t)2 * S);
+    d.C = Cd; d.M = Md; d.lam4 = l4; d.pq = pqd;
+    d.rowc = cv.take<float>((size_t)N1 * ldd);
+    d.colc = cv.take<float>((size_t)N2 * ldd);
+    d.line = cv.take<float>((size_t)lines * 3 * ldd);
+    d.shot = cv.take<float>((size_t)3 * ldd);
+    d.ecnt = cv.take<int>((size_t)lines * ldd);
+    d.eU = cv.take<double>((size_t)N1 * ldd);
+    d.eC = cv.take<double>((size_t)N1 * ldd);
+    return cv.off + kAlign;
+  };
+  cudaStream_t st = c->stream;
+  c->fwd_valid = false;
+  c->have_eval = false;
+  if (c->dbm_mem && c->dbm.N1 != N1) {  // new shape: reallocate (the captured step
+    cudaStreamSynchronize(st);           // holds the old pointers)
+    drop_graph(c);
+    cudaFree(c->dbm_mem);
+    c->dbm_mem = nullptr;
+  }
+  if (!c->dbm_mem) {
+    DbmDev probe;
+    const size_t bytes = carve_dbm(nullptr, probe);
+    if (c->cfg.mem_cap_bytes && c->ws_bytes + bytes > c->cfg.mem_cap_bytes)
+      return fail(c, CPRA_ENOMEM, "cpra_set_dbm: exceeds mem_cap_bytes");
+    if (cudaMalloc(&c->dbm_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->dbm_mem = nullptr;
+      return fail(c, CPRA_ENOMEM, "cpra_set_dbm: device allocation failed");
+    }
+    c->dbm_bytes = (int64_t)bytes;
+    DbmDev d;
+    d.N1 = N1;
+    d.N2 = N2;
+    d.ld = ldd;
+    carve_dbm(c->dbm_mem, d);
+    c->dbm = d;
+  }
+  cpra_status s = cuda_check(c, cudaMemsetAsync(c->dbm_mem, 0, (size_t)c->dbm_bytes, st), "memset");
+  const size_t row = sizeof(float) * (size_t)S;
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpy2DAsync(const_cast<float*>(c->dbm.C), sizeof(float) * ldd, C,
+                                        sizeof(float) * ld, row, c->N, cudaMemcpyHostToDevice, st),
+                   "DBM rewards");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpy2DAsync(const_cast<float*>(c->dbm.M), sizeof(float) * ldd, M,
+                                        sizeof(float) * ld, row, c->N, cudaMemcpyHostToDevice, st),
+                   "DBM fields");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpyAsync(const_cast<float*>(c->dbm.lam4), lam4, sizeof(float) * 4 * S,
+                                      cudaMemcpyHostToDevice, st), "DBM lambdas");
+  if (s == CPRA_OK)
+    s = cuda_check(c, cudaMemcpyAsync(const_cast<float*>(c->dbm.pq), pq, sizeof(float) * 2 * S,
+                                      cudaMemcpyHostToDevice, st), "DBM p, q");
   if (s == CPRA_OK) s = cuda_check(c, cudaStreamSynchronize(st), "sync");
   return s;
 }

@@ -7,7 +7,11 @@
 // objective-functions):
 //   MIS     cost -= P_is, pen += 1/2 P_is Q_is, dR/dP = -1 + lambda_s Q_is
 //   MaxCut  cost += P_is Q_is - deg_i P_is,      dR/dP = 2 Q_is - deg_i
-//   ann    += 1 - (2P_is - 1)^alpha,  dR/dP += -2 alpha gamma (2P_is-1)^(alpha-1)
+//   DBM     cost -= C_is P_is, pen = the shot's penalty (added once, at row
+//           0), dR/dP from the line sums of k_dbm.cu; no neighbour gathers
+//   ann    += 1 - (2P_is - 1)^alpha (summed as 4P(1-P)(1 + t^2 + ...), t = 2P-1,
+//             free of cancellation near 0 and 1),
+//             dR/dP += -2 alpha gamma (2P_is-1)^(alpha-1)
 //   Psi: row mean / variance over the S shots by lane shuffles (O(S) per
 //   node, Prop. 3.2), dR/dP += nu * dPsi/dP_is
 // writes G = dR/dP * P (1 - P) (the sigmoid head's dR/dZ2), and packs the
@@ -122,8 +126,22 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
     const int ch = c * LPR + sub;
     if (ch >= nchG) continue;
     float out[4];
-    float wv[4] = {1.f, 1.f, 1.f, 1.f};  // weighted MIS: w_is of this chunk
+    float wv[4] = {1.f, 1.f, 1.f, 1.f};  // weighted MIS: w_is; DBM: C_is
     if (PROBLEM == 0 && a.w) load16(a.w + i * a.ldw + ch * 4, wv);
+    // DBM: dl/dx = -C + rowc + colc + b + d M from the step's line sums
+    float dm[4], dr[4], dk[4], db[4], dd[4], dp[4];
+    if constexpr (PROBLEM == 2) {
+      const int64_t ld = a.dbm.ld;
+      const int64_t r = i / a.dbm.N2;
+      const int64_t k = i - r * a.dbm.N2;
+      load16(a.dbm.C + i * ld + ch * 4, wv);
+      load16(a.dbm.M + i * ld + ch * 4, dm);
+      load16(a.dbm.rowc + r * ld + ch * 4, dr);
+      load16(a.dbm.colc + k * ld + ch * 4, dk);
+      load16(a.dbm.shot + ch * 4, db);
+      load16(a.dbm.shot + ld + ch * 4, dd);
+      load16(a.dbm.shot + 2 * ld + ch * 4, dp);
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int s = ch * 4 + e;
@@ -131,6 +149,8 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
       float g;
       if (PROBLEM == 0) {
         g = -wv[e] + lam[c][e] * qv;
+      } else if (PROBLEM == 2) {
+        g = -wv[e] + dr[e] + dk[e] + db[e] + dd[e] * dm[e];
       } else {
         g = 2.f * qv - deg;
       }
@@ -148,10 +168,25 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
         if (PROBLEM == 0) {
           acc.pc[c][e] -= wv[e] * pv;
           acc.pp[c][e] += 0.5f * pv * qv;
+        } else if (PROBLEM == 2) {
+          acc.pc[c][e] -= wv[e] * pv;
+          if (i == 0) acc.pp[c][e] += dp[e];  // the shot's whole penalty, once
         } else {
           acc.pc[c][e] += pv * qv - deg * pv;
         }
-        acc.pa[c][e] += 1.f - tp * t;
+        // 1 - t^alpha = (1 - t^2)(1 + t^2 + ... + t^(alpha-2)) with
+        // 1 - t^2 = 4 P (1 - P): no cancellation as P approaches 0 or 1
+        float an = 4.f * pv * (1.f - pv);
+        if (a.alpha != 2) {
+          const float t2 = t * t;
+          float pw = 1.f, sm = 1.f;
+          for (int r = 2; r < a.alpha; r += 2) {
+            pw *= t2;
+            sm += pw;
+          }
+          an *= sm;
+        }
+        acc.pa[c][e] += an;
         acc.pg[c][e] += g;
       } else {
         g = 0.f;
@@ -273,8 +308,11 @@ loss_kernel(LossArgs a) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) q[c][e] = 0.f;
 
-    const int beg = a.rowptr[i];
-    const int end = a.rowptr[i + 1];
+    int beg = 0, end = 0;
+    if constexpr (PROBLEM != 2) {  // DBM needs no neighbour rows
+      beg = a.rowptr[i];
+      end = a.rowptr[i + 1];
+    }
     for (int eb = beg; eb < end; eb += LPR) {
       const int ee = eb + sub;
       const int jl = (ee < end) ? a.col[ee] : 0;
@@ -581,7 +619,7 @@ int dispatch_loss(const LossArgs& a, int nch, int max_grid, int staged_grid, cud
   if (nch <= 4) return launch_loss_t<4, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 8) return launch_loss_t<8, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
   if (nch <= 16) return launch_loss_t<16, 1, PROBLEM, TG, DO_LOSS>(a, max_grid, st);
-  if constexpr (DO_LOSS) {
+  if constexpr (DO_LOSS && PROBLEM != 2) {
     int g = -1;
     if (nch <= 32) g = launch_staged_t<1, PROBLEM, TG>(a, staged_grid, st);
     else if (nch <= 64) g = launch_staged_t<2, PROBLEM, TG>(a, staged_grid, st);
@@ -611,6 +649,10 @@ int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st) {
   if (a.problem == 0) {
     if (a.dg == DT_BF16) return dispatch_loss<0, bf16, true>(a, nch, max_grid, staged_grid, st);
     return dispatch_loss<0, float, true>(a, nch, max_grid, staged_grid, st);
+  }
+  if (a.problem == 2) {
+    if (a.dg == DT_BF16) return dispatch_loss<2, bf16, true>(a, nch, max_grid, staged_grid, st);
+    return dispatch_loss<2, float, true>(a, nch, max_grid, staged_grid, st);
   }
   if (a.dg == DT_BF16) return dispatch_loss<1, bf16, true>(a, nch, max_grid, staged_grid, st);
   return dispatch_loss<1, float, true>(a, nch, max_grid, staged_grid, st);
@@ -649,13 +691,6 @@ void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
   colsum_finalize_kernel<<<grid, block, 0, st>>>(part, nblocks, pstride, ncols, out, out2,
                                                  copy_from, copy_n, err_flag);
 }
-
-struct ShotEvalRec {
-  long long objective;
-  long long violations;
-  double qubo;
-  double value;
-};
 
 __global__ void eval_finalize_kernel(const unsigned long long* __restrict__ cnt, int S,
                                      int problem, const float* __restrict__ lambda,

@@ -82,6 +82,24 @@ int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st);
 
 // ---------------------------------------------------------------- loss
 // Fused SpMM + relaxed loss + rounding/evaluation (see cpra_op_loss).
+// Diverse bipartite matching (Eq. matching-cost-function): x_ij is node
+// i*N2 + j; every per-shot array has row stride ld (>= S, a multiple of 4).
+struct DbmDev {
+  int N1 = 0, N2 = 0;
+  int64_t ld = 0;
+  const float* C = nullptr;     // N x ld: reward C_ij of shot s's instance
+  const float* M = nullptr;     // N x ld: 1 if i and j are in different fields
+  const float* lam4 = nullptr;  // S x 4: lambda_1..4 of shot s
+  const float* pq = nullptr;    // S x 2: p, q of shot s
+  float* rowc = nullptr;        // N1 x ld: lambda_1 1[R_is > 1], R_is = sum_j P_(ij)s
+  float* colc = nullptr;        // N2 x ld: lambda_2 1[K_js > 1], K_js = sum_i P_(ij)s
+  float* line = nullptr;        // (N1+N2) x 3 x ld: per-line ReLU excess, T and U parts
+  float* shot = nullptr;        // 3 x ld: b_s, d_s, pen_s (dl/dx = -C + rowc + colc + b + d M)
+  int* ecnt = nullptr;          // (N1+N2) x ld: pairs per line of the rounded shots
+  double* eU = nullptr;         // N1 x ld: sum_j M x per row line
+  double* eC = nullptr;         // N1 x ld: sum_j C x per row line
+};
+
 struct LossArgs {
   int64_t N = 0;
   int S = 0;
@@ -102,6 +120,7 @@ struct LossArgs {
   int64_t pstride = 0;
   int do_loss = 1;               // 0: rounding bits only
   int* err_flag = nullptr;       // device word; bit 1 set if a bounded wait gave up
+  DbmDev dbm;                    // problem 2 (DBM): instance and per-step line sums
 };
 int64_t loss_pstride(int S);
 constexpr int kLossMaxGrid = 2048;
@@ -122,6 +141,13 @@ void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
                       int problem, unsigned long long* counters, int max_grid, cudaStream_t st);
 
+// Device image of cpra_shot_eval.
+struct ShotEvalRec {
+  long long objective;
+  long long violations;
+  double qubo;
+  double value;
+};
 // Per-shot records from the integer counters: objective, violations and the
 // FP64 qubo value; pair-Hamming total copied out.
 void eval_finalize(const unsigned long long* counters, int S, int problem,
@@ -132,6 +158,19 @@ void eval_finalize(const unsigned long long* counters, int S, int problem,
 // fixed order.
 void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* w, int64_t ldw,
                            double* part, int max_blocks, double* value, cudaStream_t st);
+
+// ---------------------------------------------------------------- DBM (k_dbm.cu)
+// Line sums of the relaxed matching P (FP32, N x ldp): R, K, T, U in the
+// fixed orders j (rows), i (columns), then rows / columns ascending; fills
+// d.rowc, d.colc and d.shot for the loss kernel's problem-2 epilogue.
+void dbm_sums_launch(const DbmDev& d, int S, const float* P, int64_t ldp, cudaStream_t st);
+// Exact evaluation of the rounded matchings (bits N x ceil(S/32)): per shot
+// objective = pairs, violations = rows and columns with more than one pair
+// plus the failed diversity constraints, value = sum C x and qubo = l(x) in
+// FP64; records as in eval_finalize, pair-Hamming total from counters[2S].
+void dbm_eval_launch(const DbmDev& d, int S, const uint32_t* bits,
+                     const unsigned long long* counters, void* out_records,
+                     long long* pair_hamming, cudaStream_t st);
 
 // ---------------------------------------------------------------- GEMM
 enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT = 3,

@@ -302,3 +302,15 @@ def dbm_lambda_grid(n: int = 11):
     a, b in {2^0, ..., 2^(n-1)}; returns [n*n, 4]."""
     v = 2.0 ** np.arange(n)
     return np.array([(a, a, b, b) for a in v for b in v], dtype=np.float32)
+
+
+def dbm_shots(N1: int, N2: int, instances, lam4, pq):
+    """Per-shot arrays of a DBM run from a list of instances (C, M) [N] each
+    and per-shot penalties lam4 [S, 4] and shares pq [S, 2]: shot s uses
+    instance s mod len(instances).  Returns C [N, S], M [N, S], lam4, pq."""
+    lam4 = np.asarray(lam4, dtype=np.float32)
+    S = lam4.shape[0]
+    C = np.stack([instances[s % len(instances)][0] for s in range(S)], axis=1)
+    M = np.stack([instances[s % len(instances)][1] for s in range(S)], axis=1)
+    return (C.astype(np.float32), M.astype(np.float32), lam4,
+            np.broadcast_to(np.asarray(pq, dtype=np.float32), (S, 2)).copy())

@@ -111,6 +111,31 @@ def test_op_loss_matches_oracle(case, grad_kind):
     assert np.array_equal(bh, O.pack_bits(O.round_solutions(P)))
 
 
+@pytest.mark.parametrize("alpha", [2, 4])
+def test_op_loss_annealing_term_near_integral_P(alpha):
+    """Late in annealing P sits next to 0 or 1, where 1 - (2P-1)^alpha is a
+    difference of nearly equal numbers; the per-shot annealing sums (which
+    the early-stopping threshold reads) keep FP32 relative accuracy there."""
+    N, S = 20000, 16
+    rp, col = I.random_regular_graph(N, 3, seed=8)
+    rng = np.random.default_rng(2)
+    eps = np.float32(10.0) ** rng.uniform(-6, -3, size=(N, S)).astype(np.float32)
+    P = np.where(rng.random((N, S)) < 0.5, eps, np.float32(1) - eps).astype(np.float32)
+    ld = rup(S, 16)
+    rpd, cold = dev_csr(rp, col)
+    Pd = torch.zeros((N, ld), device="cuda")
+    Pd[:, :S] = torch.from_numpy(P).cuda()
+    G = torch.zeros((N, ld), device="cuda")
+    terms = torch.zeros(4 * S + 1, device="cuda")
+    scratch = torch.empty(cpra.cpra_op_loss_scratch_bytes(N, S), dtype=torch.uint8, device="cuda")
+    lam = torch.ones(S, device="cuda")
+    cpra.cpra_op_loss(rpd, cold, Pd, lam, O.MIS, alpha, -1.0, 0.0, O.DIV_STD, 0, G, None, terms,
+                      scratch)
+    ann = terms.cpu().numpy()[2 * S:3 * S].astype(np.float64)
+    ref = O.loss_terms(O.Graph(rp, col), P, np.ones(S), O.MIS, alpha)["ann"]
+    assert np.max(np.abs(ann - ref) / ref) <= 1e-5
+
+
 def test_op_loss_constant_rows_have_zero_diversity_gradient():
     N, S = 64, 16
     rp, col = I.random_regular_graph(N, 3, seed=3)
