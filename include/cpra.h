@@ -68,8 +68,8 @@ enum { CPRA_DIV_STD = 0, CPRA_DIV_VAR = 1 };          /* Psi form               
 typedef struct cpra_config {
   int32_t problem;          /* CPRA_MIS, CPRA_MAXCUT, CPRA_WMIS or CPRA_DBM       */
   int32_t S;                /* shots = columns of P, 1..1024                      */
-  int32_t H0;               /* node-embedding width (multiple of 16, <= 1024)    */
-  int32_t H1;               /* hidden width (multiple of 16, <= 1024)            */
+  int32_t H0;               /* node-embedding width (multiple of 16, <= 4096)    */
+  int32_t H1;               /* hidden width (multiple of 16, <= 4096)            */
   int32_t alpha;            /* even exponent of the annealing term, >= 2          */
   int32_t precision;        /* CPRA_FP32: all FP32; CPRA_BF16: dense layers BF16
                                on tensor cores with FP32 accumulation             */

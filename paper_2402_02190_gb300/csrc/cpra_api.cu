@@ -199,8 +199,8 @@ std::string validate_config(const cpra_config* cfg) {
       cfg->problem != CPRA_DBM)
     return "problem must be MIS, MAXCUT, WMIS or DBM";
   if (cfg->S < 1 || cfg->S > 1024) return "S must be in [1, 1024]";
-  if (cfg->H0 < 16 || cfg->H0 > 1024 || cfg->H0 % 16) return "H0 must be a multiple of 16 in [16, 1024]";
-  if (cfg->H1 < 16 || cfg->H1 > 1024 || cfg->H1 % 16) return "H1 must be a multiple of 16 in [16, 1024]";
+  if (cfg->H0 < 16 || cfg->H0 > 4096 || cfg->H0 % 16) return "H0 must be a multiple of 16 in [16, 4096]";
+  if (cfg->H1 < 16 || cfg->H1 > 4096 || cfg->H1 % 16) return "H1 must be a multiple of 16 in [16, 4096]";
   if (cfg->alpha < 2 || cfg->alpha > 32 || cfg->alpha % 2) return "alpha must be even, 2..32";
   if (cfg->precision != CPRA_FP32 && cfg->precision != CPRA_BF16) return "precision must be FP32 or BF16";
   if (cfg->diversity_kind != CPRA_DIV_STD && cfg->diversity_kind != CPRA_DIV_VAR) return "bad diversity_kind";
@@ -247,6 +247,21 @@ std::string validate_graph(int64_t N, const int64_t* rowptr, const int32_t* col)
   return "";
 }
 
+// Split count of a weight gradient C[M x Nc] summed over the N node rows:
+// about two tiles per SM, at least 256 rows per split (CUDA-core path); the
+// tensor-core path splits into at most num_sms / tiles slices of its own
+// 256 x 256 tiles.
+int64_t wgrad_splits(const cpra_ctx* c, int64_t M, int64_t Nc) {
+  const int64_t tiles = ((M + 63) / 64) * ((Nc + 63) / 64);
+  int64_t splits = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + tiles - 1) / tiles);
+  return std::min<int64_t>(splits, std::max<int64_t>(1, c->N / 256));
+}
+size_t wgrad_part_floats(const cpra_ctx* c, int64_t M, int64_t Nc) {
+  const int64_t tc_tiles = ((M + 255) / 256) * ((Nc + 255) / 256);
+  const int64_t tc = std::max<int64_t>(1, (int64_t)c->num_sms / tc_tiles);
+  return (size_t)(M * Nc * std::max(wgrad_splits(c, M, Nc), tc));
+}
+
 // Carves every device buffer; with base == nullptr only sizes the layout.
 size_t carve(cpra_ctx* c, void* base) {
   Carver cv(base);
@@ -289,9 +304,10 @@ size_t carve(cpra_ctx* c, void* base) {
   c->eval_rec = cv.take<cpra_shot_eval>(c->S);
   c->ham_d = cv.take<long long>(1);
   c->colsum_part = cv.take<float>((size_t)kLossMaxGrid * c->H1);
-  // split-K partials: up to 4*num_sms slabs of the larger weight gradient
-  const size_t slab = std::max((size_t)c->S_pad * 2 * c->H1, (size_t)c->H1 * 2 * c->H0);
-  c->wg_part_floats = slab * (size_t)(4 * c->num_sms);
+  // split-K partials: room for the split count either weight-gradient path
+  // picks (wgrad_splits) for the larger of the two gradients
+  c->wg_part_floats = std::max(wgrad_part_floats(c, c->S_pad, 2 * c->H1),
+                               wgrad_part_floats(c, c->H1, 2 * c->H0));
   c->wg_part = cv.take<float>(c->wg_part_floats);
   c->err_flag = cv.take<int>(4);
   c->es = cv.take<EarlyStopState>(1);
@@ -429,9 +445,7 @@ void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_
   g.epi = EPI_PARTIAL;
   g.out0 = c->wg_part;
   g.ld0 = Nc;
-  const int64_t tiles = ((int64_t)(M + 63) / 64) * ((Nc + 63) / 64);
-  int64_t splits = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + tiles - 1) / tiles);
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, c->N / 256));
+  int64_t splits = wgrad_splits(c, M, Nc);
   const int64_t cap = (int64_t)(c->wg_part_floats / ((size_t)M * Nc));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, cap));
   g.splits = (int)splits;
@@ -460,7 +474,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.X = c->XM; a.ldx = 2 * H0; a.Y = act_off(c->XM, H0, c); a.ldy = 2 * H0; a.mean = 1;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-    c->launches += 1;
+    c->launches += spmm_slices(a.H);
   }
   {  // H1 = relu([X0|M1] Wcat1^T + b1)
     Region r(c, K_GEMM_L1);
@@ -481,7 +495,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.X = c->HM; a.ldx = 2 * H1; a.Y = act_off(c->HM, H1, c); a.ldy = 2 * H1; a.mean = 1;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-    c->launches += 1;
+    c->launches += spmm_slices(a.H);
   }
   {  // P = sigmoid([H1|M2] Wcat2^T + b2)
     Region r(c, K_GEMM_L2);
@@ -614,7 +628,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     if (grid < 0) return CPRA_EINVAL;
     colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
                     c->stream);
-    c->launches += 2;
+    c->launches += spmm_slices(H1) + 1;
   }
   {
     Region r(c, K_WGRAD1);  // dWcat1 = G_Z1^T [X0|M1]
@@ -654,7 +668,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       }
       a.dx = c->act_dt; a.dy = DT_F32; a.err_flag = c->err_flag;
       if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-      c->launches += 1;
+      c->launches += spmm_slices(a.H);
     }
     // With recompute the gradient block overwrote the embedding copy that
     // the forward reads; the fused update rewrites it, otherwise restore it.

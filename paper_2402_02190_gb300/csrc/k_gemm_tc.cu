@@ -2,10 +2,14 @@
 // tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in TMEM) fed by
 // TMA (cp.async.bulk.tensor, 128-byte swizzle), sm_103a.
 //
-// C[M x Nc] = A[M x K] * B[Nc x K]^T with both operands K-major.  The weight
-// operand B (at most 256 x 256 here) stays resident in shared memory for the
-// whole persistent kernel; 128-row tiles of A stream through a ring of
-// shared-memory stages.  Roles per CTA (one CTA per SM):
+// C[M x Nc] = A[M x K] * B[Nc x K]^T with both operands K-major.  Each CTA
+// owns one n tile of width BN (the last one may be ragged: rows of B past Nc
+// read as zeros and their columns are not stored) and a strided set of
+// 128-row m tiles.  When the tile's weight slice B[BN x K] fits in shared
+// memory it stays resident for the whole persistent kernel and only A
+// streams through the ring of shared-memory stages; for wide layers (large
+// K) each stage carries the matching 64-column block of B as well.  Roles
+// per CTA (one CTA per SM):
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocation + MMA issuer (one elected lane)
 //   warps 2..17 epilogue: TMEM -> registers -> bias / activation / split ->
@@ -138,6 +142,7 @@ struct TcParams {
   int Nc = 0, K = 0, n_kb = 0, BN = 0, n_tiles_n = 0, stages = 0, tmem_cols = 0, acc_stride = 0;
   int64_t m_tiles = 0;
   uint32_t idesc = 0;
+  int stream_b = 0;  // 1: B blocks stream with the A stages (weights not resident)
   int epi = 0;
   const float* bias = nullptr;
   void* out0 = nullptr;
@@ -279,9 +284,12 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const uint32_t b_kb_bytes = static_cast<uint32_t>(p.BN) * kBK * 2;
+  const bool sb_mode = p.stream_b != 0;
+  // resident: [B: n_kb blocks][A stages]; streaming: stages of [A block | B block]
+  const uint32_t stage_bytes = kStageBytes + (sb_mode ? b_kb_bytes : 0u);
   uint8_t* Bs = smem;
-  uint8_t* As = Bs + static_cast<size_t>(p.n_kb) * b_kb_bytes;
-  uint8_t* Stg = As + static_cast<size_t>(p.stages) * kStageBytes;
+  uint8_t* As = sb_mode ? smem : Bs + static_cast<size_t>(p.n_kb) * b_kb_bytes;
+  uint8_t* Stg = As + static_cast<size_t>(p.stages) * stage_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(Stg + kStgTotal);
   uint64_t* empty = full + p.stages;
   uint64_t* bfull = empty + p.stages;
@@ -333,9 +341,11 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // ---------------- TMA producer ----------------
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-      mbar_expect_tx(bfull, static_cast<uint32_t>(p.n_kb) * b_kb_bytes);
-      for (int kb = 0; kb < p.n_kb; ++kb)
-        tma_load_2d(Bs + static_cast<size_t>(kb) * b_kb_bytes, &tmB, bfull, kb * kBK, n0);
+      if (!sb_mode) {
+        mbar_expect_tx(bfull, static_cast<uint32_t>(p.n_kb) * b_kb_bytes);
+        for (int kb = 0; kb < p.n_kb; ++kb)
+          tma_load_2d(Bs + static_cast<size_t>(kb) * b_kb_bytes, &tmB, bfull, kb * kBK, n0);
+      }
       uint32_t armed = 0;        // bit s: stage s has been armed at least once
       uint32_t last_par = 0;     // bit s: parity of the last arming of stage s
       int stage = 0;
@@ -348,9 +358,10 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             ok = false;
             break;
           }
-          mbar_expect_tx(full + stage, kStageBytes);
-          tma_load_2d(As + static_cast<size_t>(stage) * kStageBytes, &tmA, full + stage, kb * kBK,
-                      static_cast<int>(mt * kBM));
+          uint8_t* st = As + static_cast<size_t>(stage) * stage_bytes;
+          mbar_expect_tx(full + stage, stage_bytes);
+          tma_load_2d(st, &tmA, full + stage, kb * kBK, static_cast<int>(mt * kBM));
+          if (sb_mode) tma_load_2d(st + kStageBytes, &tmB, full + stage, kb * kBK, n0);
           armed |= 1u << stage;
           last_par = (last_par & ~(1u << stage)) | (phase << stage);
           if (++stage == p.stages) {
@@ -367,15 +378,17 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, (last_par >> s) & 1u); ++it) {
             }
           }
-        const uint32_t a = smem_u32(bfull);
-        for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, 0); ++it) {
+        if (!sb_mode) {
+          const uint32_t a = smem_u32(bfull);
+          for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, 0); ++it) {
+          }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      bool ok = mbar_wait(bfull, 0, abort_flag);
+      bool ok = sb_mode || mbar_wait(bfull, 0, abort_flag);
       if (!ok) give_up();
       int stage = 0;
       uint32_t phase = 0;
@@ -396,8 +409,9 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(As + static_cast<size_t>(stage) * kStageBytes);
-          const uint32_t b0 = smem_u32(Bs + static_cast<size_t>(kb) * b_kb_bytes);
+          const uint32_t a0 = smem_u32(As + static_cast<size_t>(stage) * stage_bytes);
+          const uint32_t b0 = sb_mode ? a0 + kStageBytes
+                                      : smem_u32(Bs + static_cast<size_t>(kb) * b_kb_bytes);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
             umma_bf16(d_tmem, desc_kmajor_sw128(a0 + 32 * k), desc_kmajor_sw128(b0 + 32 * k),
@@ -446,6 +460,7 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int h = 0; h < 2; ++h) {
           if (h == 1 && !two) break;
           const int c = c2 + 16 * h;
+          if (n0 + c >= p.Nc) continue;  // ragged last n tile: nothing stored past Nc
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
@@ -778,12 +793,39 @@ size_t tc_smem_need(int bn, int64_t K) {
   return 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal + 2 * kStageBytes + 256;
 }
 
-// Widest n tile (a multiple of 16 dividing Nc, at most 256) whose weight
-// slice stays resident in shared memory; 0 if none does.
-int pick_bn(int Nc, int64_t K) {
-  for (int bn = Nc < 256 ? Nc : 256; bn >= 16; bn -= 16)
-    if (Nc % bn == 0 && tc_smem_need(bn, K) <= static_cast<size_t>(g_max_smem)) return bn;
-  return 0;
+// Shared memory with BN columns when the weights stream with the A stages
+// (two stages at least).
+size_t tc_stream_smem_need(int bn) {
+  return 1024 + kStgTotal + 2 * (static_cast<size_t>(kStageBytes) + static_cast<size_t>(bn) * kBK * 2) +
+         256;
+}
+
+struct NPlan {
+  int bn = 0;
+  bool stream = false;
+};
+
+// n tile of a product with Nc (a multiple of 16) output columns: the widest
+// multiple of 16 up to min(Nc, 256) whose weight slice stays resident, as
+// long as that keeps the tile at least min(Nc, 128) wide (narrower tiles
+// waste the tensor pipe); otherwise the widest tile with streamed weights.
+// The last tile may be ragged.  bn = 0: no plan fits.
+NPlan plan_n(int Nc, int64_t K) {
+  NPlan pl;
+  const int cap = Nc < 256 ? Nc : 256;
+  const int want = cap < 128 ? cap : 128;
+  for (int bn = cap; bn >= want; bn -= 16)
+    if (tc_smem_need(bn, K) <= static_cast<size_t>(g_max_smem)) {
+      pl.bn = bn;
+      return pl;
+    }
+  for (int bn = cap; bn >= 16; bn -= 16)
+    if (tc_stream_smem_need(bn) <= static_cast<size_t>(g_max_smem)) {
+      pl.bn = bn;
+      pl.stream = true;
+      return pl;
+    }
+  return pl;
 }
 
 }  // namespace
@@ -803,7 +845,7 @@ bool tc_gemm_supported(const GemmArgs& g) {
       g.epi != EPI_RELU_BITS && g.epi != EPI_BIAS)
     return false;
   if (g.K < kBK || g.K % 8 || g.lda % 8 || g.ldb % 8) return false;
-  if (g.Nc % 16 || pick_bn(g.Nc, g.K) == 0) return false;
+  if (g.Nc % 16 || plan_n(g.Nc, g.K).bn == 0) return false;
   if (g.epi == EPI_SPLIT && g.split % 16) return false;
   if ((g.epi != EPI_RELU_BITS && g.ld0 % 8) || (g.epi == EPI_SPLIT && g.ld1 % 8)) return false;
   return true;
@@ -814,16 +856,20 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.M = g.M;
   p.Nc = g.Nc;
   p.K = static_cast<int>(g.K);
-  p.BN = pick_bn(g.Nc, g.K);
-  p.n_tiles_n = g.Nc / p.BN;
+  const NPlan pl = plan_n(g.Nc, g.K);
+  p.BN = pl.bn;
+  p.stream_b = pl.stream ? 1 : 0;
+  p.n_tiles_n = (g.Nc + p.BN - 1) / p.BN;
   p.n_kb = (p.K + kBK - 1) / kBK;
   p.m_tiles = (g.M + kBM - 1) / kBM;
-  const size_t b_bytes = static_cast<size_t>(p.n_kb) * p.BN * kBK * 2;
+  const size_t b_kb = static_cast<size_t>(p.BN) * kBK * 2;
+  const size_t b_bytes = pl.stream ? 0 : static_cast<size_t>(p.n_kb) * b_kb;
+  const size_t stage_bytes = kStageBytes + (pl.stream ? b_kb : 0);
   const size_t fixed = 1024 + b_bytes + kStgTotal + 256;
-  int stages = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / kStageBytes);
+  int stages = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / stage_bytes);
   stages = stages > 6 ? 6 : stages;
   p.stages = stages;
-  size_t smem = fixed + static_cast<size_t>(stages) * kStageBytes;
+  size_t smem = fixed + static_cast<size_t>(stages) * stage_bytes;
   // at least 120 KB so that only one CTA (and one TMEM allocation) fits per SM
   if (smem < 120 * 1024) smem = 120 * 1024;
   p.acc_stride = (p.BN + 31) / 32 * 32;

@@ -187,7 +187,7 @@ spmm_rows_kernel(SpmmArgs a) {
         // o is dR/dh^0 for this chunk: one Adam step on the FP32 master row,
         // its moments, and the activation-dtype copy the forward reads (the
         // copy is rewritten even when early stopping froze the update)
-        const int64_t off = i * a.H + ch * VEC;
+        const int64_t off = i * a.lde + ch * VEC;
         float th[VEC], m[VEC], vv[VEC];
 #pragma unroll
         for (int q = 0; q < VEC; q += 4) {
@@ -243,7 +243,7 @@ spmm_rows_kernel(SpmmArgs a) {
     for (int col = threadIdx.x; col < a.H; col += blockDim.x) {
       float t = 0.f;
       for (int w = 0; w < nwarps; ++w) t += red[w * a.H + col];
-      a.colsum_partials[(int64_t)blockIdx.x * a.H + col] = t;
+      a.colsum_partials[(int64_t)blockIdx.x * a.ldcs + col] = t;
     }
   }
 }
@@ -279,7 +279,12 @@ int launch_t(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   if (grid > resident) grid = resident;
   if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
-  kernel<<<(int)grid, threads, smem, st>>>(a);
+  if (a.grid > 0) grid = a.grid;
+  if (a.plan_only) return (int)grid;
+  SpmmArgs b = a;
+  if (b.lde == 0) b.lde = b.H;
+  if (b.ldcs == 0) b.ldcs = b.H;
+  kernel<<<(int)grid, threads, smem, st>>>(b);
   return (int)grid;
 }
 
@@ -298,7 +303,8 @@ int dispatch_lpr(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) 
 
 }  // namespace
 
-int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
+namespace {
+int spmm_launch_one(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   const bool add = a.add != nullptr, mask = a.mask != nullptr, cs = a.colsum_partials != nullptr;
   const bool same = a.dx == a.dy;
   if (a.adam && (a.mean || !add || mask || cs)) return -1;
@@ -327,6 +333,53 @@ int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
                            : dispatch_lpr<float, float, KIND_ADD>(a, num_sms, max_grid, st);
   }
   return -1;  // operand set not used by the training step
+}
+}  // namespace
+
+// Rows wider than kSliceH columns run as column slices of at most kSliceH
+// (every operand set is column-separable: the aggregation, the mask, the
+// column sums and the embedding update act column by column), all with one
+// grid so that the column-sum partial rows line up.
+int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
+  if (a.H <= kSliceH) return spmm_launch_one(a, num_sms, max_grid, st);
+  if (a.H % 16) return -1;
+  const int nsl = (a.H + kSliceH - 1) / kSliceH;
+  const int chunks = a.H / 16;
+  auto slice = [&](int k) {
+    const int c0 = 16 * (chunks * k / nsl), c1 = 16 * (chunks * (k + 1) / nsl);
+    SpmmArgs b = a;
+    const size_t ex = a.dx == DT_BF16 ? 2 : 4, ey = a.dy == DT_BF16 ? 2 : 4;
+    b.H = c1 - c0;
+    b.X = static_cast<const char*>(a.X) + c0 * ex;
+    if (a.Y) b.Y = static_cast<char*>(a.Y) + c0 * ey;
+    if (a.add) b.add = static_cast<const char*>(a.add) + c0 * ex;
+    if (a.mask) b.mask = static_cast<const char*>(a.mask) + c0 * ex;
+    if (a.mask_bits) b.mask_bits = a.mask_bits + c0 / 16;
+    if (a.colsum_partials) b.colsum_partials = a.colsum_partials + c0;
+    b.ldcs = a.ldcs ? a.ldcs : a.H;
+    if (a.emb) {
+      b.lde = a.lde ? a.lde : a.H;
+      b.emb = a.emb + c0;
+      b.emb_m = a.emb_m + c0;
+      b.emb_v = a.emb_v + c0;
+      b.shadow = static_cast<char*>(a.shadow) + c0 * ex;
+    }
+    return b;
+  };
+  int grid = 0;
+  for (int k = 0; k < nsl; ++k) {
+    SpmmArgs b = slice(k);
+    b.plan_only = 1;
+    const int g = spmm_launch_one(b, num_sms, max_grid, st);
+    if (g < 0) return -1;
+    grid = (k == 0 || g < grid) ? g : grid;
+  }
+  for (int k = 0; k < nsl; ++k) {
+    SpmmArgs b = slice(k);
+    b.grid = grid;
+    if (spmm_launch_one(b, num_sms, max_grid, st) < 0) return -1;
+  }
+  return grid;
 }
 
 }  // namespace cpra

@@ -70,8 +70,15 @@ struct SpmmArgs {
   void* shadow = nullptr;
   int64_t lds = 0;
   float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
+  int64_t lde = 0;    // row stride of emb / emb_m / emb_v (0: H)
+  int64_t ldcs = 0;   // row stride of colsum_partials (0: H)
+  int grid = 0;       // > 0: launch exactly this grid
+  int plan_only = 0;  // 1: return the grid without launching
 };
+constexpr int kSliceH = 1024;  // widest row one SpMM launch covers
+inline int spmm_slices(int H) { return H <= kSliceH ? 1 : (H + kSliceH - 1) / kSliceH; }
 // Five operand sets are supported (the ones the training step uses):
+// rows wider than kSliceH run as column slices with one common grid.
 // mean aggregation (no add/mask/colsum, dy == dx), add + mask + colsum with
 // mean = 0 (dy == dx; the mask as values or as bits), add only with mean = 0
 // (dy = f32), and the latter with the fused embedding update (adam = 1).  The grid is the

@@ -206,3 +206,28 @@ def test_errors():
     with pytest.raises(cpra.CpraError):
         m.set_dbm(4, C, C, lam4, pq)
     m.close()
+
+
+def test_step_at_the_papers_width_matches_oracle():
+    """The paper's DBM network is 2500 wide (H0 = H1; here 2512, the next
+    multiple of 16) on the 11 x 11 penalty grid: wide aggregations in column
+    slices and the dense layers with streamed weights, BF16 form."""
+    out, ref, rec, ham, bits, inst, g, theta, X0, gamma, S, H = _run_step(
+        cpra.BF16, N1=20, N2=25, S=121, H=2512, seed=3)
+    tol = 2e-2
+    assert np.abs(out["P"] - ref["P"]).max() <= tol
+    t, rt = out["terms"], ref["terms"]
+    norm = np.abs(rt["cost"]) + np.abs(rt["pen"]) + abs(gamma) * rt["ann"]
+    L = t[:S] + t[S:2 * S] + gamma * t[2 * S:3 * S]
+    Lr = rt["cost"] + rt["pen"] + gamma * rt["ann"]
+    assert np.max(np.abs(L - Lr) / norm) <= tol
+    lay = I.param_layout(H, H, S)
+    for name in ("Wcat1", "b1", "Wcat2", "b2"):
+        off, shape = lay[name]
+        n = int(np.prod(shape))
+        a, b = out["grad"][off:off + n], ref["grads"]["theta"][off:off + n]
+        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), name
+    x = I.unpack_bits(bits, S).astype(np.int64)
+    ev = O.integer_eval(g, x, np.ones(S), O.DBM, inst=inst)
+    assert np.array_equal(rec["violations"], ev["violations"])
+    assert np.allclose(rec["qubo"], ev["qubo"], rtol=1e-12, atol=1e-9)
