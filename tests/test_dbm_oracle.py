@@ -119,3 +119,31 @@ def test_constraint_graph():
     edges = set(zip(np.repeat(np.arange(20), np.diff(rp)).tolist(), col.tolist()))
     assert all((j, i) in edges for i, j in edges)
     assert (0 * 5 + 1, 0) in edges and (1 * 5 + 0, 0) in edges and (1 * 5 + 1, 0) not in edges
+
+
+@pytest.mark.parametrize("N1,N2,seed", [(3, 3, 1), (3, 4, 2), (4, 3, 5)])
+def test_reference_optimum_matches_enumeration(N1, N2, seed):
+    """The exact optimum the DBM runs are scored against (scipy's MILP) equals
+    enumeration of all pair sets on tiny instances."""
+    pytest.importorskip("scipy.optimize", minversion=None)
+    from scipy import optimize
+    if not hasattr(optimize, "milp"):
+        pytest.skip("scipy without milp")
+    from paper_2402_02190_gb300 import dbm
+    Cv, Mv, p, q = I.dbm_instance(N1, N2, seed=seed, n_fields=2)
+    C, M = Cv.astype(np.float64), Mv.astype(np.float64)
+    best = 0.0
+    for xbits in itertools.product([0, 1], repeat=N1 * N2):
+        X = np.array(xbits).reshape(N1, N2)
+        if (X.sum(axis=1) > 1).any() or (X.sum(axis=0) > 1).any():
+            continue
+        T, U = X.sum(), (M.reshape(N1, N2) * X).sum()
+        if p * T - U > 0 or q * T - (T - U) > 0:
+            continue
+        best = max(best, float((C.reshape(N1, N2) * X).sum()))
+    val, x = dbm.best_diverse_matching(C, M, N1, N2, p, q)
+    assert val == pytest.approx(best, abs=1e-9)
+    # the returned matching is feasible and has that reward
+    inst = dict(N1=N1, N2=N2, C=C[:, None], M=M[:, None], lam4=np.ones((1, 4)), pq=np.array([[p, q]]))
+    ev = O.integer_eval(_graph(N1, N2), x[:, None], np.ones(1), O.DBM, inst=inst)
+    assert ev["violations"][0] == 0 and ev["value"][0] == pytest.approx(best, abs=1e-9)
