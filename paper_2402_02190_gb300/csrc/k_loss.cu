@@ -18,6 +18,9 @@
 // rounding x = 1[P > 0.5f] (App. C.2) of row i into bits; the exact integer
 // evaluation of those bits runs in k_eval.cu.
 //
+// The epilogue is instantiated per problem: 0 MIS, 1 MaxCut, 2 DBM,
+// 3 weighted MIS (node weights w in place of the unit reward).
+//
 // Two kernels share the per-row epilogue:
 //   loss_kernel         rows of up to 64 shots (and bit packing alone):
 //                       segments of LPR lanes per row, neighbour rows
@@ -121,13 +124,16 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
     if (sub == 0) acc.psi += -(float)S * (float)S * var;
   }
   const float c_ann = -2.f * (float)a.alpha * gamma;
+  const bool alpha2 = a.alpha == 2;
+  const bool use_nu = a.nu != 0.f;
+  const bool scale_g = a.grad_kind == 0;
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int ch = c * LPR + sub;
     if (ch >= nchG) continue;
     float out[4];
     float wv[4] = {1.f, 1.f, 1.f, 1.f};  // weighted MIS: w_is; DBM: C_is
-    if (PROBLEM == 0 && a.w) load16(a.w + i * a.ldw + ch * 4, wv);
+    if constexpr (PROBLEM == 3) load16(a.w + i * a.ldw + ch * 4, wv);
     // DBM: dl/dx = -C + rowc + colc + b + d M from the step's line sums
     float dm[4], dr[4], dk[4], db[4], dd[4], dp[4];
     if constexpr (PROBLEM == 2) {
@@ -147,46 +153,46 @@ __device__ __forceinline__ void row_epilogue(const LossArgs& a, int64_t i, int s
       const int s = ch * 4 + e;
       const float pv = p[c][e], qv = q[c][e];
       float g;
-      if (PROBLEM == 0) {
+      if constexpr (PROBLEM == 0 || PROBLEM == 3) {
         g = -wv[e] + lam[c][e] * qv;
-      } else if (PROBLEM == 2) {
+      } else if constexpr (PROBLEM == 2) {
         g = -wv[e] + dr[e] + dk[e] + db[e] + dd[e] * dm[e];
       } else {
         g = 2.f * qv - deg;
       }
       const float t = 2.f * pv - 1.f;
-      float tp = t;  // t^(alpha-1)
-      if (a.alpha != 2)
-        for (int r = 2; r < a.alpha; ++r) tp *= t;
+      const float pq1 = pv * (1.f - pv);  // the sigmoid derivative P(1-P)
+      // t^(alpha-1) = t (t^2)^((alpha-2)/2); the annealing term
+      // 1 - t^alpha = (1 - t^2)(1 + t^2 + ... + t^(alpha-2)) with
+      // 1 - t^2 = 4 P (1 - P): no cancellation as P approaches 0 or 1
+      float tp = t, sm4 = 4.f;
+      if (!alpha2) {
+        const float t2 = t * t;
+        float pw = 1.f, sm = 1.f;
+        for (int r = 2; r < a.alpha; r += 2) {
+          pw *= t2;
+          sm += pw;
+        }
+        tp = t * pw;
+        sm4 = 4.f * sm;
+      }
       g += c_ann * tp;
-      if (a.nu != 0.f) {
+      if (use_nu) {
         const float d = pv - mean;
         g += a.nu * ((a.div_kind == 0) ? -d * rstd : -2.f * (float)S * d);
       }
-      if (a.grad_kind == 0) g *= pv * (1.f - pv);
+      if (scale_g) g *= pq1;
       if (s < S) {
-        if (PROBLEM == 0) {
+        if constexpr (PROBLEM == 0 || PROBLEM == 3) {
           acc.pc[c][e] -= wv[e] * pv;
           acc.pp[c][e] += 0.5f * pv * qv;
-        } else if (PROBLEM == 2) {
+        } else if constexpr (PROBLEM == 2) {
           acc.pc[c][e] -= wv[e] * pv;
           if (i == 0) acc.pp[c][e] += dp[e];  // the shot's whole penalty, once
         } else {
           acc.pc[c][e] += pv * qv - deg * pv;
         }
-        // 1 - t^alpha = (1 - t^2)(1 + t^2 + ... + t^(alpha-2)) with
-        // 1 - t^2 = 4 P (1 - P): no cancellation as P approaches 0 or 1
-        float an = 4.f * pv * (1.f - pv);
-        if (a.alpha != 2) {
-          const float t2 = t * t;
-          float pw = 1.f, sm = 1.f;
-          for (int r = 2; r < a.alpha; r += 2) {
-            pw *= t2;
-            sm += pw;
-          }
-          an *= sm;
-        }
-        acc.pa[c][e] += an;
+        acc.pa[c][e] = fmaf(sm4, pq1, acc.pa[c][e]);
         acc.pg[c][e] += g;
       } else {
         g = 0.f;
@@ -261,7 +267,7 @@ __device__ __forceinline__ void load_lambda(const LossArgs& a, int sub, float (&
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int s = (c * LPR + sub) * 4 + e;
-      lam[c][e] = (PROBLEM == 0 && s < a.S) ? a.lambda[s] : 0.f;
+      lam[c][e] = ((PROBLEM == 0 || PROBLEM == 3) && s < a.S) ? a.lambda[s] : 0.f;
     }
 }
 
@@ -646,6 +652,10 @@ int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st) {
     return dispatch_loss<0, float, false>(a, nch, max_grid, staged_grid, st);
   }
   const int nch = (int)(a.ldg / 4);
+  if (a.problem == 0 && a.w) {  // weighted MIS
+    if (a.dg == DT_BF16) return dispatch_loss<3, bf16, true>(a, nch, max_grid, staged_grid, st);
+    return dispatch_loss<3, float, true>(a, nch, max_grid, staged_grid, st);
+  }
   if (a.problem == 0) {
     if (a.dg == DT_BF16) return dispatch_loss<0, bf16, true>(a, nch, max_grid, staged_grid, st);
     return dispatch_loss<0, float, true>(a, nch, max_grid, staged_grid, st);
