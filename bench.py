@@ -188,6 +188,13 @@ def loss_kernel_bytes(N, nnz, S, g_bytes):
     return nnz * S * 4 + N * S * 4 + N * S * g_bytes + 4 * (N + 1) + 4 * nnz + N * ((S + 31) // 32) * 4
 
 
+def loss_compulsory_bytes(N, nnz, S, g_bytes):
+    """The same launch's compulsory bytes: every input read once (P, CSR) and
+    every output written once (G, bits), as if every neighbour row were
+    served from on-chip memory."""
+    return N * S * 4 + N * S * g_bytes + 4 * (N + 1) + 4 * nnz + N * ((S + 31) // 32) * 4
+
+
 # ---------------------------------------------------------------- CPU oracle
 def oracle_steps(w, n_nodes, steps, seed=0):
     """Runs `steps` FP64 oracle steps on the bounded sample; returns
@@ -225,19 +232,24 @@ def cpu_baseline_child(argv):
                       "nnz": nnz, "N": n}))
 
 
-def run_cpu_baseline(wname, budget=15.0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def run_cpu_baseline(wname, budget=15.0, threads=1):
+    """The oracle on the host cores in a child process whose BLAS uses
+    `threads` threads (the oracle's dense products; its sparse scatter-adds
+    stay on one thread)."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", wname,
                         str(budget)], capture_output=True, text=True, env=env, timeout=600)
     if r.returncode != 0:
-        return {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": METRIC, "cores": threads, "kind": "oracle",
                 "sample": "failed: " + r.stderr.strip()[-200:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     w = WORKLOADS[wname]
-    return {"value": d["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+    how = "single-threaded numpy" if threads == 1 else f"numpy with {threads} BLAS threads"
+    return {"value": d["value"], "unit": METRIC, "cores": threads, "kind": "oracle",
             "sample": (f"{d['steps']} FP64 oracle step(s) on a {w['graph']} graph N={d['N']} "
                        f"(degree {w['d']}, nnz={d['nnz']}), S={w['S']}, H={w['H']}, same problem; "
-                       f"{d['seconds']:.1f} s single-threaded numpy")}
+                       f"{d['seconds']:.1f} s {how}")}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -335,6 +347,7 @@ def run_gpu(args):
     loss_ms, loss_n = prof.get("loss_fused", (0.0, 0))
     g_bytes = 2 if w["precision"] == 1 else 4
     alg = loss_kernel_bytes(N, nnz, S, g_bytes)
+    comp = loss_compulsory_bytes(N, nnz, S, g_bytes)
     achieved = alg / (loss_ms / loss_n / 1e3) / 1e9 if loss_n else None
     traffic = ncu_traffic("loss_fused", args.workload)
     line = {
@@ -356,6 +369,12 @@ def run_gpu(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "alg_bytes_per_launch": alg, "avg_ms": loss_ms / loss_n if loss_n else None,
+                     # a second line: the bound if no neighbour row were re-read
+                     # (the gathers' amplification over it is alg / compulsory)
+                     "compulsory": {"bytes_per_launch": comp,
+                                    "achieved": comp / (loss_ms / loss_n / 1e3) / 1e9 if loss_n else None,
+                                    "frac": (comp / (loss_ms / loss_n / 1e3) / 1e9 / peak) if loss_n else None,
+                                    "gather_amplification": alg / comp},
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": replica_throughput(world, nnz * S * args.steps, e2e_s), "unit": METRIC,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -373,6 +392,10 @@ def run_gpu(args):
     }
     if rank == 0:
         line["cpu_baseline"] = run_cpu_baseline(args.workload) if not args.no_cpu else None
+        if not args.no_cpu and world == 1:
+            # the same oracle with every host core behind its dense products
+            cores = len(os.sched_getaffinity(0))
+            line["cpu_baseline_all_cores"] = run_cpu_baseline(args.workload, 10.0, cores)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
