@@ -128,6 +128,12 @@ struct cpra_ctx {
   DbmDev dbm;                     // matching instances (problem DBM)
   void* dbm_mem = nullptr;        // own cudaMalloc behind dbm, null until cpra_set_dbm
   int64_t dbm_bytes = 0;
+  // the graph is the matching's constraint graph: aggregations through line
+  // sums line_R [N1 x ldl], line_K [N2 x ldl] (in the DBM allocation)
+  bool line_agg = false;
+  float* line_R = nullptr;
+  float* line_K = nullptr;
+  int64_t ldl = 0;
   void* init_logits = nullptr;    // warm start: N x S_pad act dtype, own cudaMalloc
   StepScalars* sc = nullptr;      // per-step gamma / bias corrections (device)
   // one captured training step, replayed by cpra_steps / cpra_solve
@@ -459,6 +465,19 @@ void wgrad(cpra_ctx* c, const void* A, int64_t lda, int M, const void* B, int64_
   c->launches += 2;
 }
 
+// On the matching constraint graph an aggregation reads line sums of its
+// operand instead of gathering neighbour rows: form them first.
+void use_line_sums(cpra_ctx* c, SpmmArgs& a) {
+  if (!c->line_agg) return;
+  dbm_line_sums_launch(c->dbm.N1, c->dbm.N2, a.H, a.X, a.ldx, a.dx, c->line_R, c->line_K, c->ldl,
+                       c->stream);
+  a.line_r = c->line_R;
+  a.line_k = c->line_K;
+  a.line_n2 = c->dbm.N2;
+  a.ldl = c->ldl;
+  c->launches += 1;
+}
+
 cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
                                  const StepScalars* sc = nullptr) {
   const bool dbm = c->cfg.problem == CPRA_DBM;
@@ -473,6 +492,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.N = N; a.H = H0; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
     a.X = c->XM; a.ldx = 2 * H0; a.Y = act_off(c->XM, H0, c); a.ldy = 2 * H0; a.mean = 1;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
+    use_line_sums(c, a);
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
     c->launches += spmm_slices(a.H);
   }
@@ -494,6 +514,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.N = N; a.H = H1; a.rowptr = c->rowptr; a.col = c->col; a.inv_deg = c->inv_deg;
     a.X = c->HM; a.ldx = 2 * H1; a.Y = act_off(c->HM, H1, c); a.ldy = 2 * H1; a.mean = 1;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
+    use_line_sums(c, a);
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
     c->launches += spmm_slices(a.H);
   }
@@ -543,8 +564,9 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     Region r(c, K_EVAL);
     cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
                     c->stream);
-    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits, c->cfg.problem == CPRA_MAXCUT ? 1 : 0,
-                     c->counters,
+    // DBM: the pair counts come from the line counts below, so no edges here
+    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits,
+                     dbm ? 2 : c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->counters,
                      c->num_sms * 8, c->stream);
     if (c->w_d) {  // weighted MIS: the value of each shot in weight units
       weighted_value_launch(N, c->S, c->xbits, c->w_d, c->S_pad, c->wv_part, kWvBlocks,
@@ -624,6 +646,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     a.Y = c->GHM; a.ldy = 2 * H1; a.mean = 0;
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     a.colsum_partials = c->colsum_part;
+    use_line_sums(c, a);
     const int grid = spmm_launch(a, c->num_sms, std::min(max_grid, kLossMaxGrid), c->stream);
     if (grid < 0) return CPRA_EINVAL;
     colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
@@ -667,7 +690,8 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
         adam_bias(c, &a.bc1, &a.bc2);
       }
       a.dx = c->act_dt; a.dy = DT_F32; a.err_flag = c->err_flag;
-      if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
+      use_line_sums(c, a);
+    if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
       c->launches += spmm_slices(a.H);
     }
     // With recompute the gradient block overwrote the embedding copy that
@@ -1365,6 +1389,30 @@ cpra_status cpra_set_node_weights(cpra_ctx* c, const float* w, int64_t ld, int32
   return s;
 }
 
+namespace {
+// Whether the CSR is the constraint graph of an N1 x N2 matching: node r*N2 + k
+// adjacent exactly to the other pairs of row r and of column k.
+bool is_constraint_graph(int N1, int N2, const int* rowptr, const int* col) {
+  const int deg = N1 + N2 - 2;
+  std::vector<int> want;
+  want.reserve(deg);
+  for (int r = 0; r < N1; ++r)
+    for (int k = 0; k < N2; ++k) {
+      const int64_t i = (int64_t)r * N2 + k;
+      if (rowptr[i + 1] - rowptr[i] != deg) return false;
+      want.clear();
+      for (int q = 0; q < N2; ++q)
+        if (q != k) want.push_back(r * N2 + q);
+      for (int q = 0; q < N1; ++q)
+        if (q != r) want.push_back(q * N2 + k);
+      std::sort(want.begin(), want.end());
+      for (int e = 0; e < deg; ++e)
+        if (col[rowptr[i] + e] != want[e]) return false;
+    }
+  return true;
+}
+}  // namespace
+
 cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M, int64_t ld,
                          const float* lam4, const float* pq) {
   if (!c) return CPRA_EINVAL;
@@ -1389,6 +1437,9 @@ cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M
   const int N2 = (int)(c->N / N1);
   const int64_t ldd = c->S_pad;
   const int lines = N1 + N2;
+  const int64_t ldl = std::max(c->H0, c->H1);
+  float* lr = nullptr;
+  float* lk = nullptr;
   // one allocation: C, M, rowc, colc, line sums, shot coefficients, eval partials
   auto carve_dbm = [&](void* base, DbmDev& d) -> size_t {
     Carver cv(base);
@@ -1404,6 +1455,8 @@ cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M
     d.ecnt = cv.take<int>((size_t)lines * ldd);
     d.eU = cv.take<double>((size_t)N1 * ldd);
     d.eC = cv.take<double>((size_t)N1 * ldd);
+    lr = cv.take<float>((size_t)N1 * ldl);
+    lk = cv.take<float>((size_t)N2 * ldl);
     return cv.off + kAlign;
   };
   cudaStream_t st = c->stream;
@@ -1432,6 +1485,19 @@ cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M
     d.ld = ldd;
     carve_dbm(c->dbm_mem, d);
     c->dbm = d;
+    c->line_R = lr;
+    c->line_K = lk;
+    c->ldl = ldl;
+    // aggregate through line sums when the graph is this matching's
+    // constraint graph (checked on a host copy of the CSR)
+    std::vector<int> rp((size_t)c->N + 1), cl((size_t)std::max<int64_t>(c->nnz, 1));
+    bool ok = cudaMemcpy(rp.data(), c->rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost) ==
+                  cudaSuccess &&
+              cudaMemcpy(cl.data(), c->col, sizeof(int) * cl.size(), cudaMemcpyDeviceToHost) ==
+                  cudaSuccess;
+    if (!ok) cudaGetLastError();
+    c->line_agg = ok && is_constraint_graph(N1, N2, rp.data(), cl.data());
+    drop_graph(c);  // the captured step (if any) has the gathered aggregations
   }
   cpra_status s = cuda_check(c, cudaMemsetAsync(c->dbm_mem, 0, (size_t)c->dbm_bytes, st), "memset");
   const size_t row = sizeof(float) * (size_t)S;

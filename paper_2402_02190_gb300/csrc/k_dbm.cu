@@ -19,6 +19,12 @@
 // The rounded matchings are evaluated exactly the same way: line counts of
 // the rounding bits, FP64 sums of C x and M x per row line, then one thread
 // per shot adds the lines in order and applies the constraints in FP64.
+//
+// The GNN's own graph, the constraint graph (pairs adjacent when they share
+// a row or a column), is aggregated through line sums as well: the
+// neighbour sum of pair (r, k) is R_r + K_k - 2 x_(r,k), with R, K the line
+// sums of the activation block (line_sums_kernel, O(N H) instead of the
+// (N1 + N2 - 2) N H of a gathered SpMM).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -144,7 +150,36 @@ __global__ void dbm_eval_finalize_kernel(DbmDev d, int S, const unsigned long lo
   out[s].value = value;
 }
 
+// One thread per (line, column): the line's sum in index order.
+template <typename TX>
+__global__ void line_sums_kernel(int N1, int N2, int H, const TX* __restrict__ X, int64_t ldx,
+                                 float* __restrict__ R, float* __restrict__ K, int64_t ldl) {
+  const int h = blockIdx.y * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const int b = blockIdx.x;
+  float t = 0.f;
+  if (b < N1) {
+    const TX* row = X + (int64_t)b * N2 * ldx + h;
+    for (int k = 0; k < N2; ++k) t += to_f(row[(int64_t)k * ldx]);
+    R[(int64_t)b * ldl + h] = t;
+  } else {
+    const int k = b - N1;
+    const TX* col = X + (int64_t)k * ldx + h;
+    for (int r = 0; r < N1; ++r) t += to_f(col[(int64_t)r * N2 * ldx]);
+    K[(int64_t)k * ldl + h] = t;
+  }
+}
+
 }  // namespace
+
+void dbm_line_sums_launch(int N1, int N2, int H, const void* X, int64_t ldx, int dx, float* R,
+                          float* K, int64_t ldl, cudaStream_t st) {
+  const dim3 grid(N1 + N2, (H + 127) / 128);
+  if (dx == DT_BF16)
+    line_sums_kernel<bf16><<<grid, 128, 0, st>>>(N1, N2, H, static_cast<const bf16*>(X), ldx, R, K, ldl);
+  else
+    line_sums_kernel<float><<<grid, 128, 0, st>>>(N1, N2, H, static_cast<const float*>(X), ldx, R, K, ldl);
+}
 
 void dbm_sums_launch(const DbmDev& d, int S, const float* P, int64_t ldp, cudaStream_t st) {
   const dim3 grid(d.N1 + d.N2, (S + kLineThreads - 1) / kLineThreads);

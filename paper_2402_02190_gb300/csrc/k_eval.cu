@@ -100,6 +100,7 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
       ppend = rowptr[i + 2 * stride + 1];
     }
     const uint32_t xi = active ? bits[i * W + sub] : 0u;
+    if constexpr (PROBLEM == 2) end = beg;  // set sizes and the Hamming sum only
     for (int eb = beg; eb < end; eb += U) {
       // lanes of the segment hold up to U neighbour indices, then every lane
       // loads its word of each neighbour j > i (each edge once, at its lower
@@ -146,7 +147,7 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) k += __shfl_xor_sync(smask, k, off);
     if (sub == 0) ham += (long long)k * (long long)(S - k);
-    if (PROBLEM == 0) {
+    if (PROBLEM != 1) {
       obj.add(xi);
       if (obj.n == kFlushAt) obj.flush(cnt_obj);
     }
@@ -179,8 +180,10 @@ void launch_g(int64_t N, int S, int W, const int* rowptr, const int* col, const 
   if (grid < 1) grid = 1;
   if (problem == 0)
     eval_bits_kernel<G, 0><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
-  else
+  else if (problem == 1)
     eval_bits_kernel<G, 1><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
+  else
+    eval_bits_kernel<G, 2><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
 }
 
 // Weighted MIS value per shot: block b sums w_is over its row range for the

@@ -37,26 +37,41 @@ __global__ void copy_rows_kernel(int64_t N, int H, const float* __restrict__ src
   }
 }
 
+// BF16 copies of the dense weights in both orientations, 32 x 32 tiles
+// through shared memory so that the transposed copies are written row by row
+// too.  Tiles t < t1 cover Wcat1 (H1 x 2H0), the rest Wcat2 padded to S_pad rows.
 __global__ void weight_shadows_kernel(const float* __restrict__ th, int H0, int H1, int S,
                                       int S_pad, bf16* W1s, bf16* W1t, bf16* W2s, bf16* W2t) {
-  const int64_t n1 = (int64_t)H1 * 2 * H0;
-  const int64_t n2 = (int64_t)S_pad * 2 * H1;
-  const float* Wcat1 = th;
-  const float* Wcat2 = th + n1 + H1;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < n1) {
-      const int o = (int)(i / (2 * H0)), k = (int)(i % (2 * H0));
-      const bf16 w = __float2bfloat16_rn(Wcat1[i]);
-      W1s[i] = w;
-      W1t[(int64_t)k * H1 + o] = w;
-    } else {
-      const int64_t j = i - n1;
-      const int s = (int)(j / (2 * H1)), k = (int)(j % (2 * H1));
-      const bf16 w = __float2bfloat16_rn(s < S ? Wcat2[(int64_t)s * 2 * H1 + k] : 0.f);
-      W2s[j] = w;
-      W2t[(int64_t)k * S_pad + s] = w;
+  __shared__ bf16 tile[32][34];
+  const int K1 = 2 * H0, K2 = 2 * H1;
+  const int tc1 = (K1 + 31) / 32, tr1 = (H1 + 31) / 32;
+  const int tc2 = (K2 + 31) / 32;
+  const int64_t t1 = (int64_t)tr1 * tc1;
+  const int64_t t = blockIdx.x;
+  const float* src;
+  bf16 *ds, *dt;
+  int rows, cols, valid_rows, tcn;
+  int64_t tt;
+  if (t < t1) {
+    src = th; ds = W1s; dt = W1t; rows = H1; valid_rows = H1; cols = K1; tt = t; tcn = tc1;
+  } else {
+    src = th + (int64_t)H1 * K1 + H1; ds = W2s; dt = W2t; rows = S_pad; valid_rows = S;
+    cols = K2; tt = t - t1; tcn = tc2;
+  }
+  const int r0 = (int)(tt / tcn) * 32, c0 = (int)(tt % tcn) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int y = ty; y < 32; y += 8) {
+    const int r = r0 + y, c = c0 + tx;
+    if (r < rows && c < cols) {
+      const bf16 w = __float2bfloat16_rn(r < valid_rows ? src[(int64_t)r * cols + c] : 0.f);
+      ds[(int64_t)r * cols + c] = w;
+      tile[y][tx] = w;
     }
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {  // transposed: row c of dt, columns r
+    const int c = c0 + y, r = r0 + tx;
+    if (r < rows && c < cols) dt[(int64_t)c * rows + r] = tile[tx][y];
   }
 }
 
@@ -235,8 +250,9 @@ void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd
 
 void weight_shadows_launch(const float* theta, int H0, int H1, int S, int S_pad, void* W1s,
                            void* W1t, void* W2s, void* W2t, cudaStream_t st) {
-  const int64_t n = (int64_t)H1 * 2 * H0 + (int64_t)S_pad * 2 * H1;
-  weight_shadows_kernel<<<grid_for(n), 256, 0, st>>>(
+  const int64_t tiles = (int64_t)((H1 + 31) / 32) * ((2 * H0 + 31) / 32) +
+                        (int64_t)((S_pad + 31) / 32) * ((2 * H1 + 31) / 32);
+  weight_shadows_kernel<<<(unsigned)tiles, 256, 0, st>>>(
       theta, H0, H1, S, S_pad, static_cast<bf16*>(W1s), static_cast<bf16*>(W1t),
       static_cast<bf16*>(W2s), static_cast<bf16*>(W2t));
 }

@@ -69,20 +69,22 @@ spmm_rows_kernel(SpmmArgs a) {
   // CSR index pipeline: the current row's range and first LPR column
   // indices, and the next row's range, are loaded one iteration ahead, so the
   // gathers never wait on an index load.
+  // Matching constraint graph (line sums given): no CSR traffic at all.
+  const bool lines = a.line_r != nullptr;
   int beg = 0, end = 0, jl = 0, pbeg = 0, pend = 0;
-  if (first < a.N) {
+  if (!lines && first < a.N) {
     beg = a.rowptr[first];
     end = a.rowptr[first + 1];
     jl = (sub < end - beg) ? a.col[beg + sub] : 0;
   }
-  if (first + stride < a.N) {
+  if (!lines && first + stride < a.N) {
     pbeg = a.rowptr[first + stride];
     pend = a.rowptr[first + stride + 1];
   }
   for (int64_t i = first; i < a.N; i += stride) {
-    const int njl = (i + stride < a.N && sub < pend - pbeg) ? a.col[pbeg + sub] : 0;
+    const int njl = (!lines && i + stride < a.N && sub < pend - pbeg) ? a.col[pbeg + sub] : 0;
     int ppbeg = 0, ppend = 0;
-    if (i + 2 * stride < a.N) {
+    if (!lines && i + 2 * stride < a.N) {
       ppbeg = a.rowptr[i + 2 * stride];
       ppend = a.rowptr[i + 2 * stride + 1];
     }
@@ -107,6 +109,30 @@ spmm_rows_kernel(SpmmArgs a) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
 
+    if (lines) {
+      // the neighbours of pair (r, k) are the other pairs of row line r and
+      // of column line k: their sum is R_r + K_k - 2 x_(r,k)
+      const int64_t r = i / a.line_n2;
+      const int64_t k = i - r * a.line_n2;
+      const float* __restrict__ LR = a.line_r + r * a.ldl;
+      const float* __restrict__ LK = a.line_k + k * a.ldl;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int ch = c * LPR + sub;
+        if (ch < nchunks) {
+          float f[VEC];
+          widen(ldg_nc16(X + i * a.ldx + ch * VEC), f, (const TX*)nullptr);
+#pragma unroll
+          for (int q = 0; q < VEC; q += 4) {
+            float lr[4], lk[4];
+            load16(LR + ch * VEC + q, lr);
+            load16(LK + ch * VEC + q, lk);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[c][q + v] = (lr[v] - f[q + v]) + (lk[v] - f[q + v]);
+          }
+        }
+      }
+    }
     for (int eb = beg; eb < end; eb += LPR) {
       const int e = eb + sub;
       const int jc = (eb == beg) ? jl : ((e < end) ? a.col[e] : 0);
@@ -356,6 +382,10 @@ int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
     if (a.mask) b.mask = static_cast<const char*>(a.mask) + c0 * ex;
     if (a.mask_bits) b.mask_bits = a.mask_bits + c0 / 16;
     if (a.colsum_partials) b.colsum_partials = a.colsum_partials + c0;
+    if (a.line_r) {
+      b.line_r = a.line_r + c0;
+      b.line_k = a.line_k + c0;
+    }
     b.ldcs = a.ldcs ? a.ldcs : a.H;
     if (a.emb) {
       b.lde = a.lde ? a.lde : a.H;

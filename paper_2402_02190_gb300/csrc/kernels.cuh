@@ -74,6 +74,14 @@ struct SpmmArgs {
   int64_t ldcs = 0;   // row stride of colsum_partials (0: H)
   int grid = 0;       // > 0: launch exactly this grid
   int plan_only = 0;  // 1: return the grid without launching
+  // The graph is the constraint graph of an N1 x N2 matching (node r*N2 + k
+  // adjacent to every other pair of row r and of column k): with line_r /
+  // line_k the FP32 line sums of X ([N1 x ldl], [N2 x ldl], dbm_line_sums_launch),
+  // the neighbour sum is read from them instead of gathered (rowptr / col unused).
+  const float* line_r = nullptr;
+  const float* line_k = nullptr;
+  int line_n2 = 0;
+  int64_t ldl = 0;
 };
 constexpr int kSliceH = 1024;  // widest row one SpMM launch covers
 inline int spmm_slices(int H) { return H <= kSliceH ? 1 : (H + kSliceH - 1) / kSliceH; }
@@ -143,8 +151,9 @@ void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
 
 // Exact integer evaluation of rounded shots from their bits (k_eval.cu):
 // adds to counters obj[S] (MIS set size / MaxCut cut edges), viol[S] (MIS
-// edges inside the set) and counters[2S] = sum_i k_i (S - k_i).  The
-// counters must be zeroed by the caller.
+// edges inside the set) and counters[2S] = sum_i k_i (S - k_i); problem 2
+// reads no edges (set sizes and the Hamming sum only).  The counters must be
+// zeroed by the caller.
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
                       int problem, unsigned long long* counters, int max_grid, cudaStream_t st);
 
@@ -175,6 +184,11 @@ void dbm_sums_launch(const DbmDev& d, int S, const float* P, int64_t ldp, cudaSt
 // objective = pairs, violations = rows and columns with more than one pair
 // plus the failed diversity constraints, value = sum C x and qubo = l(x) in
 // FP64; records as in eval_finalize, pair-Hamming total from counters[2S].
+// Line sums of an activation block X [N1*N2 x H] (dtype dx, row stride ldx)
+// in FP32: R[r*ldl + h] = sum_k X[r*N2 + k][h], K[k*ldl + h] = sum_r X[r*N2 + k][h],
+// summed in index order.
+void dbm_line_sums_launch(int N1, int N2, int H, const void* X, int64_t ldx, int dx, float* R,
+                          float* K, int64_t ldl, cudaStream_t st);
 void dbm_eval_launch(const DbmDev& d, int S, const uint32_t* bits,
                      const unsigned long long* counters, void* out_records,
                      long long* pair_hamming, cudaStream_t st);

@@ -45,9 +45,11 @@ def _inst(N1, N2, C, M, lam4, pq):
                 lam4=lam4.astype(np.float64), pq=pq.astype(np.float64))
 
 
-def _run_step(precision, N1=30, N2=20, S=40, H=32, nu=0.25, seed=2):
-    rp, col = I.dbm_graph(N1, N2)
+def _run_step(precision, N1=30, N2=20, S=40, H=32, nu=0.25, seed=2, graph="constraint"):
     N = N1 * N2
+    # the constraint graph takes the line-sum aggregations; any other graph
+    # the gathered ones
+    rp, col = I.dbm_graph(N1, N2) if graph == "constraint" else I.random_regular_graph(N, 6, seed)
     g = O.Graph(rp, col)
     C, M, lam4, pq, L0 = _mixed_shots(N1, N2, S, seed)
     theta, X0 = I.seeded_params(N, H, H, S, seed=seed + 1, weight_scale=1.5)
@@ -81,10 +83,11 @@ def _run_step(precision, N1=30, N2=20, S=40, H=32, nu=0.25, seed=2):
     return out, ref, rec, ham, bits, inst, g, theta, X0, gamma, S, H
 
 
+@pytest.mark.parametrize("graph", ["constraint", "random"])
 @pytest.mark.parametrize("precision,tol,margin,rel", [(cpra.FP32, 1e-5, 1e-3, 1e-3),
                                                      (cpra.BF16, 2e-2, 0.2, 1e-2)])
-def test_step_matches_oracle(precision, tol, margin, rel):
-    out, ref, rec, ham, bits, inst, g, theta, X0, gamma, S, H = _run_step(precision)
+def test_step_matches_oracle(precision, tol, margin, rel, graph):
+    out, ref, rec, ham, bits, inst, g, theta, X0, gamma, S, H = _run_step(precision, graph=graph)
     # every ReLU of the penalty is decided with room to spare, and both
     # branches occur (rows, columns and each diversity constraint)
     parts = O.dbm_parts(ref["P"], inst)
