@@ -808,9 +808,14 @@ struct NPlan {
 // n tile of a product with Nc (a multiple of 16) output columns: the widest
 // multiple of 16 up to min(Nc, 256) whose weight slice stays resident, as
 // long as that keeps the tile at least min(Nc, 128) wide (narrower tiles
-// waste the tensor pipe); otherwise the widest tile with streamed weights.
-// The last tile may be ragged.  bn = 0: no plan fits.
-NPlan plan_n(int Nc, int64_t K) {
+// waste the tensor pipe); otherwise streamed weights.  The last tile may be
+// ragged.  With streamed weights and M, num_sms known, the tile width (from
+// 128 to 256) minimises the persistent schedule's critical path: each n tile
+// gets floor(num_sms / n_tiles) CTAs, which take its m tiles in turn, so the
+// slowest CTA runs ceil(m_tiles / groups) tiles of cost ~ bn (a product with
+// few m tiles, like the 2500-row DBM layers, otherwise leaves SMs idle for a
+// whole tile).  bn = 0: no plan fits.
+NPlan plan_n(int Nc, int64_t K, int64_t M = 0, int num_sms = 0) {
   NPlan pl;
   const int cap = Nc < 256 ? Nc : 256;
   const int want = cap < 128 ? cap : 128;
@@ -823,8 +828,21 @@ NPlan plan_n(int Nc, int64_t K) {
     if (tc_stream_smem_need(bn) <= static_cast<size_t>(g_max_smem)) {
       pl.bn = bn;
       pl.stream = true;
-      return pl;
+      break;
     }
+  if (pl.bn == 0 || M <= 0 || num_sms <= 0) return pl;
+  const int64_t m_tiles = (M + kBM - 1) / kBM;
+  int64_t best = -1;
+  for (int bn = pl.bn; bn >= want; bn -= 16) {
+    const int64_t n_tiles = (Nc + bn - 1) / bn;
+    const int64_t groups = n_tiles >= num_sms ? 1 : num_sms / n_tiles;
+    const int64_t rounds = n_tiles > num_sms ? (n_tiles + num_sms - 1) / num_sms : 1;
+    const int64_t cost = rounds * ((m_tiles + groups - 1) / groups) * bn;
+    if (best < 0 || cost < best) {
+      best = cost;
+      pl.bn = bn;
+    }
+  }
   return pl;
 }
 
@@ -856,7 +874,7 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.M = g.M;
   p.Nc = g.Nc;
   p.K = static_cast<int>(g.K);
-  const NPlan pl = plan_n(g.Nc, g.K);
+  const NPlan pl = plan_n(g.Nc, g.K, g.M, num_sms);
   p.BN = pl.bn;
   p.stream_b = pl.stream ? 1 : 0;
   p.n_tiles_n = (g.Nc + p.BN - 1) / p.BN;
