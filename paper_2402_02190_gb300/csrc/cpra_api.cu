@@ -494,7 +494,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     use_line_sums(c, a);
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-    c->launches += spmm_slices(a.H);
+    c->launches += 1;
   }
   {  // H1 = relu([X0|M1] Wcat1^T + b1)
     Region r(c, K_GEMM_L1);
@@ -516,7 +516,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.dx = c->act_dt; a.dy = c->act_dt; a.err_flag = c->err_flag;
     use_line_sums(c, a);
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-    c->launches += spmm_slices(a.H);
+    c->launches += 1;
   }
   {  // P = sigmoid([H1|M2] Wcat2^T + b2)
     Region r(c, K_GEMM_L2);
@@ -651,7 +651,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     if (grid < 0) return CPRA_EINVAL;
     colsum_finalize(c->colsum_part, grid, H1, H1, c->grad + L.b1, nullptr, 0, 0, nullptr,
                     c->stream);
-    c->launches += spmm_slices(H1) + 1;
+    c->launches += 2;
   }
   {
     Region r(c, K_WGRAD1);  // dWcat1 = G_Z1^T [X0|M1]
@@ -692,7 +692,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       a.dx = c->act_dt; a.dy = DT_F32; a.err_flag = c->err_flag;
       use_line_sums(c, a);
     if (spmm_launch(a, c->num_sms, max_grid, c->stream) < 0) return CPRA_EINVAL;
-      c->launches += spmm_slices(a.H);
+      c->launches += 1;
     }
     // With recompute the gradient block overwrote the embedding copy that
     // the forward reads; the fused update rewrites it, otherwise restore it.

@@ -17,8 +17,30 @@ __global__ void adam_kernel(int64_t n, float* __restrict__ th, float* __restrict
     bc1 = sc->bc1;
     bc2 = sc->bc2;
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  // four parameters per thread and iteration when every array is 16-byte
+  // aligned, the remainder one at a time
+  const bool vec = ((reinterpret_cast<uintptr_t>(th) | reinterpret_cast<uintptr_t>(m) |
+                     reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(g)) & 15u) == 0;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    for (int64_t q = tid; q < n4; q += nth) {
+      float4 t4 = reinterpret_cast<float4*>(th)[q], m4 = reinterpret_cast<float4*>(m)[q];
+      float4 v4 = reinterpret_cast<float4*>(v)[q];
+      const float4 g4 = reinterpret_cast<const float4*>(g)[q];
+      t4.x = adam_update(t4.x, m4.x, v4.x, g4.x, lr, b1, b2, eps, wd, bc1, bc2);
+      t4.y = adam_update(t4.y, m4.y, v4.y, g4.y, lr, b1, b2, eps, wd, bc1, bc2);
+      t4.z = adam_update(t4.z, m4.z, v4.z, g4.z, lr, b1, b2, eps, wd, bc1, bc2);
+      t4.w = adam_update(t4.w, m4.w, v4.w, g4.w, lr, b1, b2, eps, wd, bc1, bc2);
+      reinterpret_cast<float4*>(th)[q] = t4;
+      reinterpret_cast<float4*>(m)[q] = m4;
+      reinterpret_cast<float4*>(v)[q] = v4;
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + tid; i < n; i += nth) {
     float mi = m[i], vi = v[i];
     th[i] = adam_update(th[i], mi, vi, g[i], lr, b1, b2, eps, wd, bc1, bc2);
     m[i] = mi;

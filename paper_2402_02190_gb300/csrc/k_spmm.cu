@@ -29,6 +29,28 @@ enum SpmmKind {
 template <typename TX, typename TY, int LPR, int CPL, int KIND>
 __global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_MEAN ? 6 : KIND == KIND_ADD ? 5 : 4))
 spmm_rows_kernel(SpmmArgs a) {
+  if (a.nsl > 1) {  // column slice blockIdx.y of nsl: shift every operand
+    const int chunks = a.h_full / 16, k = blockIdx.y;
+    const int c0 = 16 * (chunks * k / a.nsl), c1 = 16 * (chunks * (k + 1) / a.nsl);
+    const int ex = a.dx == DT_BF16 ? 2 : 4, ey = a.dy == DT_BF16 ? 2 : 4;
+    a.H = c1 - c0;
+    a.X = static_cast<const char*>(a.X) + (int64_t)c0 * ex;
+    if (a.Y) a.Y = static_cast<char*>(a.Y) + (int64_t)c0 * ey;
+    if (a.add) a.add = static_cast<const char*>(a.add) + (int64_t)c0 * ex;
+    if (a.mask) a.mask = static_cast<const char*>(a.mask) + (int64_t)c0 * ex;
+    if (a.mask_bits) a.mask_bits += c0 / 16;
+    if (a.colsum_partials) a.colsum_partials += c0;
+    if (a.line_r) {
+      a.line_r += c0;
+      a.line_k += c0;
+    }
+    if (a.emb) {
+      a.emb += c0;
+      a.emb_m += c0;
+      a.emb_v += c0;
+      a.shadow = static_cast<char*>(a.shadow) + (int64_t)c0 * ex;
+    }
+  }
   constexpr bool MEAN = KIND == KIND_MEAN;
   constexpr bool HAS_ADD = KIND != KIND_MEAN;
   constexpr bool HAS_MASK = KIND == KIND_ADD_MASK_COLSUM;
@@ -305,12 +327,7 @@ int launch_t(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
   if (grid > resident) grid = resident;
   if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
-  if (a.grid > 0) grid = a.grid;
-  if (a.plan_only) return (int)grid;
-  SpmmArgs b = a;
-  if (b.lde == 0) b.lde = b.H;
-  if (b.ldcs == 0) b.ldcs = b.H;
-  kernel<<<(int)grid, threads, smem, st>>>(b);
+  kernel<<<dim3((unsigned)grid, (unsigned)a.nsl), threads, smem, st>>>(a);
   return (int)grid;
 }
 
@@ -362,54 +379,21 @@ int spmm_launch_one(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t s
 }
 }  // namespace
 
-// Rows wider than kSliceH columns run as column slices of at most kSliceH
-// (every operand set is column-separable: the aggregation, the mask, the
-// column sums and the embedding update act column by column), all with one
-// grid so that the column-sum partial rows line up.
-int spmm_launch(const SpmmArgs& a, int num_sms, int max_grid, cudaStream_t st) {
-  if (a.H <= kSliceH) return spmm_launch_one(a, num_sms, max_grid, st);
-  if (a.H % 16) return -1;
-  const int nsl = (a.H + kSliceH - 1) / kSliceH;
-  const int chunks = a.H / 16;
-  auto slice = [&](int k) {
-    const int c0 = 16 * (chunks * k / nsl), c1 = 16 * (chunks * (k + 1) / nsl);
-    SpmmArgs b = a;
-    const size_t ex = a.dx == DT_BF16 ? 2 : 4, ey = a.dy == DT_BF16 ? 2 : 4;
-    b.H = c1 - c0;
-    b.X = static_cast<const char*>(a.X) + c0 * ex;
-    if (a.Y) b.Y = static_cast<char*>(a.Y) + c0 * ey;
-    if (a.add) b.add = static_cast<const char*>(a.add) + c0 * ex;
-    if (a.mask) b.mask = static_cast<const char*>(a.mask) + c0 * ex;
-    if (a.mask_bits) b.mask_bits = a.mask_bits + c0 / 16;
-    if (a.colsum_partials) b.colsum_partials = a.colsum_partials + c0;
-    if (a.line_r) {
-      b.line_r = a.line_r + c0;
-      b.line_k = a.line_k + c0;
-    }
-    b.ldcs = a.ldcs ? a.ldcs : a.H;
-    if (a.emb) {
-      b.lde = a.lde ? a.lde : a.H;
-      b.emb = a.emb + c0;
-      b.emb_m = a.emb_m + c0;
-      b.emb_v = a.emb_v + c0;
-      b.shadow = static_cast<char*>(a.shadow) + c0 * ex;
-    }
-    return b;
-  };
-  int grid = 0;
-  for (int k = 0; k < nsl; ++k) {
-    SpmmArgs b = slice(k);
-    b.plan_only = 1;
-    const int g = spmm_launch_one(b, num_sms, max_grid, st);
-    if (g < 0) return -1;
-    grid = (k == 0 || g < grid) ? g : grid;
-  }
-  for (int k = 0; k < nsl; ++k) {
-    SpmmArgs b = slice(k);
-    b.grid = grid;
-    if (spmm_launch_one(b, num_sms, max_grid, st) < 0) return -1;
-  }
-  return grid;
+// Rows wider than spmm_slice_width columns run as column slices, blockIdx.y
+// = slice, in one launch (every operand set is column-separable: the
+// aggregation, the mask, the column sums and the embedding update act column
+// by column; the column-sum partial rows of all slices share one grid).
+int spmm_launch(const SpmmArgs& a0, int num_sms, int max_grid, cudaStream_t st) {
+  SpmmArgs a = a0;
+  if (a.lde == 0) a.lde = a.H;
+  if (a.ldcs == 0) a.ldcs = a.H;
+  const int nsl = spmm_slices(a);
+  if (nsl > 1 && a.H % 16) return -1;
+  a.nsl = nsl;
+  a.h_full = a.H;
+  // the widest slice decides the lane layout and the shared memory
+  if (nsl > 1) a.H = 16 * ((a.H / 16 + nsl - 1) / nsl);
+  return spmm_launch_one(a, num_sms, max_grid, st);
 }
 
 }  // namespace cpra

@@ -72,8 +72,8 @@ struct SpmmArgs {
   float lr = 0.f, beta1 = 0.f, beta2 = 0.f, eps = 0.f, wd = 0.f, bc1 = 1.f, bc2 = 1.f;
   int64_t lde = 0;    // row stride of emb / emb_m / emb_v (0: H)
   int64_t ldcs = 0;   // row stride of colsum_partials (0: H)
-  int grid = 0;       // > 0: launch exactly this grid
-  int plan_only = 0;  // 1: return the grid without launching
+  int nsl = 1;        // column slices (set by spmm_launch)
+  int h_full = 0;     // row width before slicing (set by spmm_launch)
   // The graph is the constraint graph of an N1 x N2 matching (node r*N2 + k
   // adjacent to every other pair of row r and of column k): with line_r /
   // line_k the FP32 line sums of X ([N1 x ldl], [N2 x ldl], dbm_line_sums_launch),
@@ -84,9 +84,18 @@ struct SpmmArgs {
   int64_t ldl = 0;
 };
 constexpr int kSliceH = 1024;  // widest row one SpMM launch covers
-inline int spmm_slices(int H) { return H <= kSliceH ? 1 : (H + kSliceH - 1) / kSliceH; }
+// Column-slice width of an aggregation: with line sums (three row reads per
+// node instead of a gather) the rows are cut to one 16-byte chunk per lane,
+// so that the light per-row work runs at full occupancy.
+inline int spmm_slice_width(const SpmmArgs& a) {
+  return a.line_r ? (a.dx == DT_BF16 ? 256 : 128) : kSliceH;
+}
+inline int spmm_slices(const SpmmArgs& a) {
+  const int w = spmm_slice_width(a);
+  return a.H <= w ? 1 : (a.H + w - 1) / w;
+}
 // Five operand sets are supported (the ones the training step uses):
-// rows wider than kSliceH run as column slices with one common grid.
+// rows wider than spmm_slice_width run as column slices of one launch.
 // mean aggregation (no add/mask/colsum, dy == dx), add + mask + colsum with
 // mean = 0 (dy == dx; the mask as values or as bits), add only with mean = 0
 // (dy = f32), and the latter with the fused embedding update (adam = 1).  The grid is the
