@@ -102,11 +102,12 @@ dbm_eval_lines_kernel(DbmDev d, int S, const uint32_t* __restrict__ bits) {
     const int64_t n0 = (int64_t)b * d.N2;
     double U = 0.0, V = 0.0;
     for (int j = 0; j < d.N2; ++j) {
-      if (bit_of(bits, W, n0 + j, s)) {
-        ++cnt;
-        U += (double)d.M[(n0 + j) * ld + s];
-        V += (double)d.C[(n0 + j) * ld + s];
-      }
+      // loads independent of the bit, so that the loop's loads overlap
+      const int x = bit_of(bits, W, n0 + j, s);
+      const float m = d.M[(n0 + j) * ld + s], c = d.C[(n0 + j) * ld + s];
+      cnt += x;
+      U += x ? (double)m : 0.0;
+      V += x ? (double)c : 0.0;
     }
     d.eU[(int64_t)b * ld + s] = U;
     d.eC[(int64_t)b * ld + s] = V;
