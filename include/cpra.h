@@ -73,10 +73,11 @@ typedef struct cpra_config {
   int32_t alpha;            /* even exponent of the annealing term, >= 2          */
   int32_t precision;        /* CPRA_FP32: all FP32; CPRA_BF16: dense layers BF16
                                on tensor cores with FP32 accumulation             */
-  int32_t recompute;        /* 1: the backward recomputes the layer-1 ReLU mask
-                               from Z1 instead of keeping H1, so the activation
-                               blocks [X0|M1], [H1|M2] share memory with the
-                               gradient blocks (2 N (H0 + H1) values less)      */
+  int32_t recompute;        /* 1: H1 is not kept for the backward (only its ReLU
+                               mask, as bits written by the layer-1 GEMM), so the
+                               activation blocks [X0|M1], [H1|M2] share memory
+                               with the gradient blocks (2 N (H0 + H1) values
+                               less, N H1 / 8 bytes more)                      */
   int32_t train_embedding;  /* 1: node embeddings h^0 are trained (default)       */
   int32_t diversity_kind;   /* CPRA_DIV_STD (Eq. ...-variation) or CPRA_DIV_VAR   */
   int32_t keep_emb_grad;    /* 0 (default): cpra_step fuses the embedding Adam

@@ -52,7 +52,7 @@ const char* kKernelNames[K_COUNT_] = {
     "spmm_agg1",   "gemm_layer1", "spmm_agg2",  "gemm_layer2", "loss_fused",
     "loss_finalize", "gemm_dgrad2", "spmm_bwd2", "wgrad2",     "wgrad1",
     "gemm_dgrad1", "spmm_bwd1",   "adam",       "spmm_bwd1_adam_embedding", "round_eval",
-    "recompute_layer1_mask", "dbm_line_sums"};
+    "recompute_layer1_mask", "dbm_line_sums"};  // the mask now comes with layer 1: id unused
 
 constexpr size_t kAlign = 256;
 constexpr int kWvBlocks = 512;  // weighted-MIS value partial rows
@@ -119,7 +119,7 @@ struct cpra_ctx {
   void* GZ2 = nullptr;
   void* GHM = nullptr;   // aliases HM when recompute
   void* GXM = nullptr;   // aliases XM when recompute
-  uint16_t* relu_bits = nullptr;  // recompute: 1[Z1 > 0] as bits, N x H1/16
+  uint16_t* relu_bits = nullptr;  // recompute: 1[H1 > 0] as bits, N x H1/16 (layer-1 epilogue)
   EarlyStopState* es = nullptr;   // early-stopping monitor (device)
   float* w_d = nullptr;           // weighted MIS: node weights N x S_pad (else null)
   double* wv_part = nullptr;      // weighted MIS: per-block value partials
@@ -293,8 +293,8 @@ size_t carve(cpra_ctx* c, void* base) {
     // The layer activations [H1|M2] and [X0|M1] are dead by the time the
     // backward writes the same-shaped gradient blocks (layer-2 weight
     // gradient first, layer-1 weight gradient before dG_X0), so each pair
-    // shares one block; the ReLU mask the layer-1 adjoint needs is
-    // recomputed from Z1 as bits.
+    // shares one block; of H1 the layer-1 adjoint needs only its ReLU
+    // mask, which the layer-1 GEMM's epilogue writes as bits.
     c->GHM = c->HM;
     c->GXM = c->XM;
     c->relu_bits = cv.take<uint16_t>((size_t)N * (c->H1 / 16));
@@ -506,6 +506,9 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     g.ldb = 2 * H0; g.b_kmajor = 1;
     g.epi = EPI_BIAS_RELU; g.bias = c->theta + L.b1;
     g.out0 = c->HM; g.ld0 = 2 * H1; g.d0 = c->act_dt; g.n_valid = H1;
+    // recompute: H1's block is overwritten by the backward, so its ReLU mask
+    // (all the layer-1 adjoint needs of it) is kept as bits, 1/16 of H1
+    if (c->recompute) { g.out1 = c->relu_bits; g.ld1 = H1 / 16; }
     dense(c, g);
   }
   {  // M2 = mean_agg(H1)
@@ -621,18 +624,6 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     g.out0 = c->GHM; g.ld0 = 2 * H1; g.d0 = c->act_dt;
     g.out1 = act_off(c->GHM, H1, c); g.ld1 = 2 * H1; g.d1 = c->act_dt;
     g.row_scale = c->inv_deg; g.n_valid = 2 * H1;
-    dense(c, g);
-  }
-  if (c->recompute) {  // 1[Z1 > 0] from Z1 = [X0|M1] Wcat1^T + b1, recomputed (a7)
-    Region r(c, K_RECOMPUTE_MASK);
-    GemmArgs g;
-    g.M = N; g.Nc = H1; g.K = 2 * H0;
-    g.A = c->XM; g.lda = 2 * H0; g.da = c->act_dt; g.a_kmajor = 1;
-    if (bf) { g.B = c->W1s; g.db = DT_BF16; }
-    else { g.B = c->theta + L.wcat1; g.db = DT_F32; }
-    g.ldb = 2 * H0; g.b_kmajor = 1;
-    g.epi = EPI_RELU_BITS; g.bias = c->theta + L.b1;
-    g.out0 = c->relu_bits; g.ld0 = H1 / 16; g.d0 = c->act_dt; g.n_valid = H1;
     dense(c, g);
   }
   {  // G_Z1 = (G_H1a + sum_j G_M2_j/deg_j) * 1[H1 > 0], db1 = colsum(G_Z1)

@@ -88,9 +88,12 @@ gemm_simt_kernel(GemmArgs g) {
     __syncthreads();
   }
 
-  if (g.epi == EPI_RELU_BITS) {
+  if (g.epi == EPI_RELU_BITS || (g.epi == EPI_BIAS_RELU && g.out1)) {
     // lanes 0-15 of a warp hold row ty, lanes 16-31 row ty + 1, each 16
     // consecutive columns n0 + 16c + tx: one ballot gives both rows' masks
+    const bool only_bits = g.epi == EPI_RELU_BITS;
+    uint16_t* mb = static_cast<uint16_t*>(only_bits ? g.out0 : g.out1);
+    const int64_t ldm = only_bits ? g.ld0 : g.ld1;
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -107,11 +110,10 @@ gemm_simt_kernel(GemmArgs g) {
         }
         const unsigned b = __ballot_sync(0xffffffffu, bit);
         if (tx == 0 && m < g.M && n < g.Nc)
-          static_cast<uint16_t*>(g.out0)[m * g.ld0 + n / 16] =
-              static_cast<uint16_t>(lane >= 16 ? b >> 16 : b & 0xffffu);
+          mb[m * ldm + n / 16] = static_cast<uint16_t>(lane >= 16 ? b >> 16 : b & 0xffffu);
       }
     }
-    return;
+    if (only_bits) return;
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) {

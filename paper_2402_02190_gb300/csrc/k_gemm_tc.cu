@@ -466,6 +466,20 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
           int col;
           const int which = epilogue16<EPI>(p, row, n0 + c, v, &col);
+          if constexpr (EPI == EPI_BIAS_RELU) {
+            // optional ReLU mask of the stored activation (dtype d0) as bits
+            if (p.out1 && row < p.M) {
+              uint32_t bits = 0;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                float h = v[i];
+                if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
+                bits |= (h > 0.f ? 1u : 0u) << i;
+              }
+              static_cast<uint16_t*>(p.out1)[row * p.ld1 + (n0 + c) / 16] =
+                  static_cast<uint16_t>(bits);
+            }
+          }
           if constexpr (EPI == EPI_RELU_BITS) {
             // mask of the activation as stored in dtype d0; no tile store
             uint32_t bits = 0;

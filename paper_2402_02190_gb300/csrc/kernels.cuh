@@ -209,7 +209,8 @@ enum Epi { EPI_PARTIAL = 0, EPI_BIAS_RELU = 1, EPI_BIAS_SIGMOID = 2, EPI_SPLIT =
 //   A(m, k) = A[m*lda + k] if a_kmajor else A[k*lda + m]; same for B.
 // Epilogues:
 //   EPI_PARTIAL      out0 (f32) + z*M*ld0 <- C for split z of gridDim.z
-//   EPI_BIAS_RELU    out0[m, n] <- max(C + bias[n], 0)
+//   EPI_BIAS_RELU    out0[m, n] <- max(C + bias[n], 0); with out1 also its mask
+//                    as bits (layout of EPI_RELU_BITS, uint16 row stride ld1)
 //   EPI_BIAS         out0[m, n] <- C + bias[n] for n < n_valid, else 0
 //   EPI_BIAS_SIGMOID out0[m, n] <- 1/(1+exp(-(C + bias[n] [+ addend[m*ld_add + n]])))
 //                    for n < n_valid, else 0 (addend, dtype d_add, may be null)
