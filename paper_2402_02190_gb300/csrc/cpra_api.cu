@@ -1482,7 +1482,8 @@ cpra_status cpra_set_dbm(cpra_ctx* c, int32_t N1, const float* C, const float* M
     // aggregate through line sums when the graph is this matching's
     // constraint graph (checked on a host copy of the CSR)
     std::vector<int> rp((size_t)c->N + 1), cl((size_t)std::max<int64_t>(c->nnz, 1));
-    bool ok = cudaMemcpy(rp.data(), c->rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost) ==
+    bool ok = cudaStreamSynchronize(st) == cudaSuccess &&
+              cudaMemcpy(rp.data(), c->rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost) ==
                   cudaSuccess &&
               cudaMemcpy(cl.data(), c->col, sizeof(int) * cl.size(), cudaMemcpyDeviceToHost) ==
                   cudaSuccess;
