@@ -254,11 +254,11 @@ std::string validate_graph(int64_t N, const int64_t* rowptr, const int32_t* col)
 }
 
 // Split count of a weight gradient C[M x Nc] summed over the N node rows:
-// about two tiles per SM, at least 256 rows per split (CUDA-core path); the
-// tensor-core path splits into at most num_sms / tiles slices of its own
-// 256 x 256 tiles.
+// about two of the CUDA-core kernel's 128 x 128 tiles per SM, at least 256
+// rows per split; the tensor-core path splits into at most num_sms / tiles
+// slices of its own 256 x 256 tiles.
 int64_t wgrad_splits(const cpra_ctx* c, int64_t M, int64_t Nc) {
-  const int64_t tiles = ((M + 63) / 64) * ((Nc + 63) / 64);
+  const int64_t tiles = ((M + 127) / 128) * ((Nc + 127) / 128);
   int64_t splits = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + tiles - 1) / tiles);
   return std::min<int64_t>(splits, std::max<int64_t>(1, c->N / 256));
 }

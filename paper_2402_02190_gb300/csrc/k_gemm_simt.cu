@@ -1,8 +1,8 @@
 // CUDA-core GEMM with FP32 accumulation for the dense GCN layers (Eq. GCN
-// combine step).  Used for the all-FP32 form and as the fallback-free
-// reference shape for the tensor-core kernels: 64 x 64 output tile per block,
-// 16 x 16 threads with 4 x 4 outputs each, K staged through shared memory in
-// slices of 16.  Operands may be K-major or MN-major, FP32 or BF16.
+// combine step): the all-FP32 form and the shapes the tensor-core kernels do
+// not take.  128 x 128 output tile per block, 16 x 16 threads with 8 x 8
+// outputs each, K staged through double-buffered shared memory in slices of
+// 16.  Operands may be K-major or MN-major, FP32 or BF16.
 #include <math.h>
 
 #include "common.cuh"
@@ -12,7 +12,7 @@ namespace cpra {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BM = 128, BN = 128, BK = 16;
 
 template <typename T>
 __device__ __forceinline__ float ld_el(const void* base, int64_t idx) {
@@ -24,12 +24,61 @@ __device__ __forceinline__ void st_el(void* base, int dt, int64_t idx, float v) 
   else static_cast<float*>(base)[idx] = v;
 }
 
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(256)
+// Four consecutive values at idx (dtype dt): one vector store when the row
+// and the address allow it.
+__device__ __forceinline__ void st4(void* base, int dt, int64_t idx, const float* v, int n_ok) {
+  if (n_ok == 4) {
+    if (dt == DT_BF16) {
+      if ((idx & 3) == 0) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&lo);
+        w.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(static_cast<bf16*>(base) + idx) = w;
+        return;
+      }
+    } else if ((idx & 3) == 0) {
+      *reinterpret_cast<float4*>(static_cast<float*>(base) + idx) = make_float4(v[0], v[1], v[2], v[3]);
+      return;
+    }
+  }
+  for (int j = 0; j < n_ok; ++j) st_el(base, dt, idx + j, v[j]);
+}
+
+// One element of the epilogue (all but the partial and the split, which the
+// caller handles); n < Nc.
+__device__ __forceinline__ float epi_value(const GemmArgs& g, int64_t m, int n, int nval, float v) {
+  switch (g.epi) {
+    case EPI_BIAS_RELU:
+    case EPI_RELU_BITS:
+      v += g.bias[n];
+      return v > 0.f ? v : 0.f;
+    case EPI_BIAS:
+      return n < nval ? v + g.bias[n] : 0.f;
+    case EPI_BIAS_SIGMOID:
+      if (g.addend && n < nval)
+        v += g.d_add == DT_BF16
+                 ? __bfloat162float(static_cast<const bf16*>(g.addend)[m * g.ld_add + n])
+                 : static_cast<const float*>(g.addend)[m * g.ld_add + n];
+      return (n < nval) ? 1.0f / (1.0f + expf(-(v + g.bias[n]))) : 0.f;
+    default:
+      return v;
+  }
+}
+
+// 128 x 128 output tile per block of 256 threads; thread (tx, ty) of a
+// 16 x 16 grid owns the 8 x 8 outputs at rows {4ty, 64 + 4ty} + 0..3 and
+// columns {4tx, 64 + 4tx} + 0..3, read from shared memory as float4.  K is
+// staged in slices of 16, double-buffered: the next slice is loaded into
+// registers while the current one is multiplied.
+template <typename TA, typename TB, bool AK, bool BKM>
+__global__ void __launch_bounds__(256, 2)
 gemm_simt_kernel(GemmArgs g) {
-  __shared__ float As[BK][BM + 4];
-  __shared__ float Bs[BK][BN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
   const int nval = g.n_valid > 0 ? g.n_valid : g.Nc;
@@ -39,113 +88,149 @@ gemm_simt_kernel(GemmArgs g) {
     kbeg = per * blockIdx.z;
     kend = kbeg + per < g.K ? kbeg + per : g.K;
   }
-  float acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
 
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    // A tile: BM x BK
+  // element e of this thread's share of a 128 x 16 slice: index id = e*256 + tid,
+  // laid out so that consecutive threads read consecutive addresses
+  float ra[8], rb[8];
+  auto load = [&](int64_t k0) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int id = threadIdx.x + t * 256;
+    for (int e = 0; e < 8; ++e) {
+      const int id = e * 256 + tid;
       int mm, kk;
-      if (g.a_kmajor) { mm = id / BK; kk = id % BK; }
+      if (AK) { mm = id / BK; kk = id % BK; }
       else { kk = id / BM; mm = id % BM; }
       const int64_t m = m0 + mm, k = k0 + kk;
-      float v = 0.f;
-      if (m < g.M && k < kend)
-        v = ld_el<TA>(g.A, g.a_kmajor ? m * g.lda + k : k * g.lda + m);
-      As[kk][mm] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int id = threadIdx.x + t * 256;
-      int nn, kk;
-      if (g.b_kmajor) { nn = id / BK; kk = id % BK; }
+      ra[e] = (m < g.M && k < kend) ? ld_el<TA>(g.A, AK ? m * g.lda + k : k * g.lda + m) : 0.f;
+      int nn;
+      if (BKM) { nn = id / BK; kk = id % BK; }
       else { kk = id / BN; nn = id % BN; }
       const int n = n0 + nn;
-      const int64_t k = k0 + kk;
-      float v = 0.f;
-      if (n < nval && k < kend)
-        v = ld_el<TB>(g.B, g.b_kmajor ? (int64_t)n * g.ldb + k : k * g.ldb + n);
-      Bs[kk][nn] = v;
+      const int64_t kb = k0 + kk;
+      rb[e] = (n < nval && kb < kend)
+                  ? ld_el<TB>(g.B, BKM ? (int64_t)n * g.ldb + kb : kb * g.ldb + n)
+                  : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int id = e * 256 + tid;
+      if (AK) As[buf][id % BK][id / BK] = ra[e];
+      else As[buf][id / BM][id % BM] = ra[e];
+      if (BKM) Bs[buf][id % BK][id / BK] = rb[e];
+      else Bs[buf][id / BN][id % BN] = rb[e];
+    }
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float a[4], b[4];
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * tx]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 
+  // ReLU mask as bits: lanes 0-15 of a warp hold row 4ty + i of an even ty,
+  // lanes 16-31 the same row of the odd ty; lane tx holds columns 4tx + j of
+  // each half.  Four ballots (one per j) give both rows' 64 columns.
   if (g.epi == EPI_RELU_BITS || (g.epi == EPI_BIAS_RELU && g.out1)) {
-    // lanes 0-15 of a warp hold row ty, lanes 16-31 row ty + 1, each 16
-    // consecutive columns n0 + 16c + tx: one ballot gives both rows' masks
     const bool only_bits = g.epi == EPI_RELU_BITS;
     uint16_t* mb = static_cast<uint16_t*>(only_bits ? g.out0 : g.out1);
     const int64_t ldm = only_bits ? g.ld0 : g.ld1;
-    const int lane = threadIdx.x & 31;
+    const int lane = tid & 31;
+    const int base = lane & 16;  // this row's lanes start here
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int64_t m = m0 + ty + 16 * r;
+    for (int i = 0; i < 8; ++i) {
+      const int64_t m = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4));
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int n = n0 + tx + 16 * c;
-        bool bit = false;
-        if (m < g.M && n < g.Nc) {
-          float v = acc[r][c] + g.bias[n];
-          v = v > 0.f ? v : 0.f;
-          if (g.d0 == DT_BF16) v = __bfloat162float(__float2bfloat16_rn(v));
-          bit = v > 0.f;
+      for (int h = 0; h < 2; ++h) {
+        unsigned bal[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = n0 + 64 * h + 4 * tx + j;
+          bool bit = false;
+          if (m < g.M && n < g.Nc) {
+            float v = epi_value(g, m, n, nval, acc[i][4 * h + j]);
+            if (g.d0 == DT_BF16) v = __bfloat162float(__float2bfloat16_rn(v));
+            bit = v > 0.f;
+          }
+          bal[j] = __ballot_sync(0xffffffffu, bit);
         }
-        const unsigned b = __ballot_sync(0xffffffffu, bit);
-        if (tx == 0 && m < g.M && n < g.Nc)
-          mb[m * ldm + n / 16] = static_cast<uint16_t>(lane >= 16 ? b >> 16 : b & 0xffffu);
+        // 16-column block q of this half comes from lanes 4q .. 4q+3 (of the row)
+        if ((tx & 3) == 0) {
+          const int q = tx >> 2;
+          uint32_t word = 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) word |= ((bal[j] >> (base + 4 * q + t)) & 1u) << (4 * t + j);
+          const int nb = n0 + 64 * h + 16 * q;
+          if (m < g.M && nb < g.Nc) mb[m * ldm + nb / 16] = static_cast<uint16_t>(word);
+        }
       }
     }
     if (only_bits) return;
   }
+
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int64_t m = m0 + ty + 16 * r;
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + (i - 4));
     if (m >= g.M) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int n = n0 + tx + 16 * c;
+    for (int h = 0; h < 2; ++h) {
+      const int n = n0 + 64 * h + 4 * tx;
       if (n >= g.Nc) continue;
-      float v = acc[r][c];
+      const int n_ok = g.Nc - n < 4 ? g.Nc - n : 4;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = acc[i][4 * h + j];
       switch (g.epi) {
         case EPI_PARTIAL:
-          static_cast<float*>(g.out0)[(int64_t)blockIdx.z * g.M * g.ld0 + m * g.ld0 + n] = v;
+          st4(g.out0, DT_F32, (int64_t)blockIdx.z * g.M * g.ld0 + m * g.ld0 + n, v, n_ok);
           break;
-        case EPI_BIAS_RELU:
-          v += g.bias[n];
-          st_el(g.out0, g.d0, m * g.ld0 + n, v > 0.f ? v : 0.f);
+        case EPI_SPLIT:  // split is a multiple of 16: the four columns sit on one side
+          if (n < g.split) {
+            st4(g.out0, g.d0, m * g.ld0 + n, v, n_ok);
+          } else {
+            const float sc = g.row_scale[m];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] *= sc;
+            st4(g.out1, g.d1, m * g.ld1 + (n - g.split), v, n_ok);
+          }
           break;
-        case EPI_BIAS:
-          st_el(g.out0, g.d0, m * g.ld0 + n, n < nval ? v + g.bias[n] : 0.f);
-          break;
-        case EPI_BIAS_SIGMOID:
-          if (g.addend && n < nval)
-            v += g.d_add == DT_BF16
-                     ? __bfloat162float(static_cast<const bf16*>(g.addend)[m * g.ld_add + n])
-                     : static_cast<const float*>(g.addend)[m * g.ld_add + n];
-          v = (n < nval) ? 1.0f / (1.0f + expf(-(v + g.bias[n]))) : 0.f;
-          st_el(g.out0, g.d0, m * g.ld0 + n, v);
-          break;
-        case EPI_SPLIT:
-          if (n < g.split) st_el(g.out0, g.d0, m * g.ld0 + n, v);
-          else st_el(g.out1, g.d1, m * g.ld1 + (n - g.split), v * g.row_scale[m]);
+        default:
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < n_ok) v[j] = epi_value(g, m, n + j, nval, v[j]);
+          st4(g.out0, g.d0, m * g.ld0 + n, v, n_ok);
           break;
       }
     }
@@ -164,15 +249,26 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
 
 }  // namespace
 
+template <typename TA, typename TB>
+void launch_layout(const GemmArgs& g, dim3 grid, cudaStream_t st) {
+  if (g.a_kmajor) {
+    if (g.b_kmajor) gemm_simt_kernel<TA, TB, true, true><<<grid, 256, 0, st>>>(g);
+    else gemm_simt_kernel<TA, TB, true, false><<<grid, 256, 0, st>>>(g);
+  } else {
+    if (g.b_kmajor) gemm_simt_kernel<TA, TB, false, true><<<grid, 256, 0, st>>>(g);
+    else gemm_simt_kernel<TA, TB, false, false><<<grid, 256, 0, st>>>(g);
+  }
+}
+
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st) {
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.Nc + BN - 1) / BN),
             g.epi == EPI_PARTIAL ? (unsigned)g.splits : 1u);
   if (g.da == DT_BF16) {
-    if (g.db == DT_BF16) gemm_simt_kernel<bf16, bf16><<<grid, 256, 0, st>>>(g);
-    else gemm_simt_kernel<bf16, float><<<grid, 256, 0, st>>>(g);
+    if (g.db == DT_BF16) launch_layout<bf16, bf16>(g, grid, st);
+    else launch_layout<bf16, float>(g, grid, st);
   } else {
-    if (g.db == DT_BF16) gemm_simt_kernel<float, bf16><<<grid, 256, 0, st>>>(g);
-    else gemm_simt_kernel<float, float><<<grid, 256, 0, st>>>(g);
+    if (g.db == DT_BF16) launch_layout<float, bf16>(g, grid, st);
+    else launch_layout<float, float>(g, grid, st);
   }
 }
 

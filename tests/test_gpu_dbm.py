@@ -204,6 +204,11 @@ def test_errors():
         s.set_dbm(4, C, C + 2.0, lam4, pq)           # M outside [0, 1]
     s.set_dbm(4, C, C, lam4, pq)
     s.step(0)
+    # a different N1 reallocates the instance buffers; the 4 x 5 constraint
+    # graph is not the 5 x 4 one, so the aggregations gather again
+    s.set_dbm(5, C, C, lam4, pq)
+    s.step(1)
+    assert np.isfinite(s.P()).all()
     s.close()
     m = cpra.Solver(rp, col, lam=np.ones(8, np.float32), problem=cpra.MIS, S=8, H0=16, H1=16)
     with pytest.raises(cpra.CpraError):
