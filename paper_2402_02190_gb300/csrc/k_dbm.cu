@@ -62,18 +62,42 @@ dbm_lines_kernel(DbmDev d, int S, const float* __restrict__ P, int64_t ldp) {
   }
 }
 
+// One warp per shot: lane l takes lines l, l + 32, ... and the lanes' partial
+// sums meet in a fixed butterfly.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 __global__ void dbm_shot_kernel(DbmDev d, int S) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (s >= S) return;
   const int64_t ld = d.ld;
   float er = 0.f, ec = 0.f, T = 0.f, U = 0.f;
-  for (int b = 0; b < d.N1; ++b) {
+  for (int b = lane; b < d.N1; b += 32) {
     const float* line = d.line + (int64_t)b * 3 * ld;
     er += line[s];
     T += line[ld + s];
     U += line[2 * ld + s];
   }
-  for (int b = d.N1; b < d.N1 + d.N2; ++b) ec += d.line[(int64_t)b * 3 * ld + s];
+  for (int b = d.N1 + lane; b < d.N1 + d.N2; b += 32) ec += d.line[(int64_t)b * 3 * ld + s];
+  er = warp_sum(er);
+  T = warp_sum(T);
+  U = warp_sum(U);
+  ec = warp_sum(ec);
+  if (lane) return;
   const float l1 = d.lam4[4 * s + 0], l2 = d.lam4[4 * s + 1];
   const float l3 = d.lam4[4 * s + 2], l4 = d.lam4[4 * s + 3];
   const float p = d.pq[2 * s + 0], q = d.pq[2 * s + 1];
@@ -84,6 +108,15 @@ __global__ void dbm_shot_kernel(DbmDev d, int S) {
   d.shot[s] = a3 * p + a4 * (q - 1.f);
   d.shot[ld + s] = a4 - a3;
   d.shot[2 * ld + s] = l1 * er + l2 * ec + l3 * fmaxf(g3, 0.f) + l4 * fmaxf(g4, 0.f);
+}
+
+// hi + lo += v with the rounding error of hi + v kept in lo (TwoSum).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bp = __fadd_rn(s, -hi);
+  const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(v, -bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
 }
 
 __device__ __forceinline__ int bit_of(const uint32_t* __restrict__ bits, int W, int64_t n, int s) {
@@ -100,17 +133,19 @@ dbm_eval_lines_kernel(DbmDev d, int S, const uint32_t* __restrict__ bits) {
   int cnt = 0;
   if (b < d.N1) {
     const int64_t n0 = (int64_t)b * d.N2;
-    double U = 0.0, V = 0.0;
+    // sums of M x and C x as unevaluated FP32 pairs (hi + lo, Knuth's
+    // TwoSum at every addition): the FP64 pipe of this part is slow, and
+    // the pair carries about 48 bits, enough for the FP64 totals
+    float Uh = 0.f, Ul = 0.f, Vh = 0.f, Vl = 0.f;
     for (int j = 0; j < d.N2; ++j) {
-      // loads independent of the bit, so that the loop's loads overlap
       const int x = bit_of(bits, W, n0 + j, s);
       const float m = d.M[(n0 + j) * ld + s], c = d.C[(n0 + j) * ld + s];
       cnt += x;
-      U += x ? (double)m : 0.0;
-      V += x ? (double)c : 0.0;
+      two_sum_acc(Uh, Ul, x ? m : 0.f);
+      two_sum_acc(Vh, Vl, x ? c : 0.f);
     }
-    d.eU[(int64_t)b * ld + s] = U;
-    d.eC[(int64_t)b * ld + s] = V;
+    d.eU[(int64_t)b * ld + s] = (double)Uh + (double)Ul;
+    d.eC[(int64_t)b * ld + s] = (double)Vh + (double)Vl;
   } else {
     const int j = b - d.N1;
     for (int i = 0; i < d.N1; ++i) cnt += bit_of(bits, W, (int64_t)i * d.N2 + j, s);
@@ -120,23 +155,31 @@ dbm_eval_lines_kernel(DbmDev d, int S, const uint32_t* __restrict__ bits) {
 
 __global__ void dbm_eval_finalize_kernel(DbmDev d, int S, const unsigned long long* counters,
                                          ShotEvalRec* out, long long* ham) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s == 0 && ham) *ham = (long long)counters[2 * S];
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s == 0 && lane == 0 && ham) *ham = (long long)counters[2 * S];
   if (s >= S) return;
   const int64_t ld = d.ld;
   long long T = 0, over = 0, ex_r = 0, ex_c = 0;
   double U = 0.0, value = 0.0;
-  for (int b = 0; b < d.N1; ++b) {
+  for (int b = lane; b < d.N1; b += 32) {
     const int c = d.ecnt[(int64_t)b * ld + s];
     T += c;
     if (c > 1) { ++over; ex_r += c - 1; }
     U += d.eU[(int64_t)b * ld + s];
     value += d.eC[(int64_t)b * ld + s];
   }
-  for (int b = d.N1; b < d.N1 + d.N2; ++b) {
+  for (int b = d.N1 + lane; b < d.N1 + d.N2; b += 32) {
     const int c = d.ecnt[(int64_t)b * ld + s];
     if (c > 1) { ++over; ex_c += c - 1; }
   }
+  T = warp_sum(T);
+  over = warp_sum(over);
+  ex_r = warp_sum(ex_r);
+  ex_c = warp_sum(ex_c);
+  U = warp_sum(U);
+  value = warp_sum(value);
+  if (lane) return;
   const double p = (double)d.pq[2 * s + 0], q = (double)d.pq[2 * s + 1];
   const double Td = (double)T;
   const double g3 = p * Td - U;
@@ -185,7 +228,7 @@ void dbm_line_sums_launch(int N1, int N2, int H, const void* X, int64_t ldx, int
 void dbm_sums_launch(const DbmDev& d, int S, const float* P, int64_t ldp, cudaStream_t st) {
   const dim3 grid(d.N1 + d.N2, (S + kLineThreads - 1) / kLineThreads);
   dbm_lines_kernel<<<grid, kLineThreads, 0, st>>>(d, S, P, ldp);
-  dbm_shot_kernel<<<(S + 127) / 128, 128, 0, st>>>(d, S);
+  dbm_shot_kernel<<<(S + 3) / 4, 128, 0, st>>>(d, S);  // a warp per shot
 }
 
 void dbm_eval_launch(const DbmDev& d, int S, const uint32_t* bits,
@@ -193,7 +236,7 @@ void dbm_eval_launch(const DbmDev& d, int S, const uint32_t* bits,
                      long long* pair_hamming, cudaStream_t st) {
   const dim3 grid(d.N1 + d.N2, (S + kLineThreads - 1) / kLineThreads);
   dbm_eval_lines_kernel<<<grid, kLineThreads, 0, st>>>(d, S, bits);
-  dbm_eval_finalize_kernel<<<(S + 127) / 128, 128, 0, st>>>(
+  dbm_eval_finalize_kernel<<<(S + 3) / 4, 128, 0, st>>>(  // a warp per shot
       d, S, counters, static_cast<ShotEvalRec*>(out_records), pair_hamming);
 }
 
