@@ -171,15 +171,24 @@ namespace {
 __global__ void early_stop_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
                                   int S, float tol, int patience, float ann_below,
                                   const StepScalars* sc, EarlyStopState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || st->stopped) return;
+  // the per-shot values in parallel (they do not depend on one another),
+  // then the two running sums in shot order on one thread
+  __shared__ double ls_s[1024], an_s[1024];
+  if (st->stopped) return;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    double ls = (double)terms[s];
+    if (lambda) ls = __dadd_rn(ls, __dmul_rn((double)lambda[s], (double)terms[S + s]));
+    ls_s[s] = ls;
+    an_s[s] = (double)terms[2 * S + s];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   const float gamma = sc->gamma;
   const long long t = sc->t, updates = sc->updates;
   double l = 0.0, ann = 0.0;
   for (int s = 0; s < S; ++s) {
-    double ls = (double)terms[s];
-    if (lambda) ls = __dadd_rn(ls, __dmul_rn((double)lambda[s], (double)terms[S + s]));
-    l = __dadd_rn(l, ls);
-    ann = __dadd_rn(ann, (double)terms[2 * S + s]);
+    l = __dadd_rn(l, ls_s[s]);
+    ann = __dadd_rn(ann, an_s[s]);
   }
   const double phi = __dmul_rn((double)gamma, ann);
   if (ann_below > 0.f && ann < (double)ann_below) {  // the annealing term has vanished
@@ -206,7 +215,7 @@ __global__ void early_stop_kernel(const float* __restrict__ terms, const float* 
 void early_stop_launch(const float* terms, const float* lambda, int S, float tol, int patience,
                        float ann_below, const StepScalars* sc, EarlyStopState* st,
                        cudaStream_t stream) {
-  early_stop_kernel<<<1, 32, 0, stream>>>(terms, lambda, S, tol, patience, ann_below, sc, st);
+  early_stop_kernel<<<1, 256, 0, stream>>>(terms, lambda, S, tol, patience, ann_below, sc, st);
 }
 
 namespace {
