@@ -1035,7 +1035,11 @@ int tc_wgrad_launch(const GemmArgs& g, int num_sms, size_t part_floats, float* d
   size_t smem = 1024 + static_cast<size_t>(s.stages) * s.stage_bytes + 256;
   if (smem < 120 * 1024) smem = 120 * 1024;
   const int grid = tiles * p.splits;
+  // one split into a destination with row stride Nc: no partials to add
+  const bool direct = p.splits == 1 && ldo == p.Nc;
+  if (direct) p.part = dst;
   tc_wgrad_kernel<<<grid, kThreads, smem, st>>>(ta, tb, p);
+  if (direct) return 1;
   splitk_reduce(p.part, p.splits, p.M, p.Nc, p.Nc, dst, ldo, st);
   return 2;
 }
