@@ -147,3 +147,35 @@ def test_reference_optimum_matches_enumeration(N1, N2, seed):
     inst = dict(N1=N1, N2=N2, C=C[:, None], M=M[:, None], lam4=np.ones((1, 4)), pq=np.array([[p, q]]))
     ev = O.integer_eval(_graph(N1, N2), x[:, None], np.ones(1), O.DBM, inst=inst)
     assert ev["violations"][0] == 0 and ev["value"][0] == pytest.approx(best, abs=1e-9)
+
+
+def test_run_layouts():
+    """The shot layouts of the DBM runs: the 11 x 11 grid of (a, a, b, b) over
+    powers of two on one instance, and one instance per shot with the fixed
+    (2, 2, 12, 12) of the multi-instance run."""
+    from paper_2402_02190_gb300 import dbm
+    Cv, Mv, p, q = I.dbm_instance(5, 4, seed=3)
+    C, M, lam4, pq = dbm.penalty_grid_shots(5, 4, Cv, Mv, p, q)
+    assert C.shape == M.shape == (20, 121) and lam4.shape == (121, 4) and pq.shape == (121, 2)
+    assert np.array_equal(C, np.repeat(Cv[:, None], 121, axis=1))
+    vals = 2.0 ** np.arange(11)
+    assert set(lam4[:, 0]) == set(vals) and np.array_equal(lam4[:, 0], lam4[:, 1])
+    assert np.array_equal(lam4[:, 2], lam4[:, 3])
+    assert len({(a, b) for a, _, b, _ in lam4}) == 121
+    insts = [I.dbm_instance(5, 4, seed=k)[:2] for k in range(7)]
+    C, M, lam4, pq = dbm.multi_instance_shots(5, 4, insts, pq=(0.05, 0.05))
+    assert C.shape == (20, 7)
+    for s in range(7):
+        assert np.array_equal(C[:, s], insts[s][0]) and np.array_equal(M[:, s], insts[s][1])
+    assert np.all(lam4 == np.array([2, 2, 12, 12], np.float32)) and np.all(pq == 0.05)
+    # field indicators are 0/1 and rewards lie in [0, 1)
+    assert set(np.unique(Mv)) <= {0.0, 1.0} and Cv.min() >= 0 and Cv.max() < 1
+
+
+def test_apr_marks_shots_without_a_feasible_matching():
+    from paper_2402_02190_gb300 import dbm
+    best = np.zeros(3, dtype=[("objective", "i8"), ("violations", "i8"), ("qubo", "f8"), ("value", "f8")])
+    best["objective"] = [4, -1, 0]
+    best["value"] = [9.0, -1.0, 0.0]
+    a = dbm.apr(best, [10.0, 10.0, 10.0])
+    assert a[0] == pytest.approx(0.9) and np.isnan(a[1]) and a[2] == 0.0
