@@ -204,11 +204,13 @@ __global__ void line_sums_kernel(int N1, int N2, int H, const TX* __restrict__ X
   float t = 0.f;
   if (b < N1) {
     const TX* row = X + (int64_t)b * N2 * ldx + h;
+#pragma unroll 10
     for (int k = 0; k < N2; ++k) t += to_f(row[(int64_t)k * ldx]);
     R[(int64_t)b * ldl + h] = t;
   } else {
     const int k = b - N1;
     const TX* col = X + (int64_t)k * ldx + h;
+#pragma unroll 10
     for (int r = 0; r < N1; ++r) t += to_f(col[(int64_t)r * N2 * ldx]);
     K[(int64_t)k * ldl + h] = t;
   }
