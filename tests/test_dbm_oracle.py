@@ -179,3 +179,22 @@ def test_apr_marks_shots_without_a_feasible_matching():
     best["value"] = [9.0, -1.0, 0.0]
     a = dbm.apr(best, [10.0, 10.0, 10.0])
     assert a[0] == pytest.approx(0.9) and np.isnan(a[1]) and a[2] == 0.0
+
+
+@pytest.mark.parametrize("N1,N2", [(1, 4), (3, 5), (6, 2)])
+def test_constraint_graph_aggregation_by_line_sums(N1, N2):
+    """On the matching's constraint graph the neighbour sum of pair (r, k) is
+    its row line's sum plus its column line's sum minus twice its own value
+    (the identity the line-sum aggregation of the library relies on), and the
+    adjoint aggregation equals the forward one (constant degree, symmetric A)."""
+    g = _graph(N1, N2)
+    rng = np.random.default_rng(N1 * 10 + N2)
+    X = rng.normal(size=(N1 * N2, 7))
+    Xr = X.reshape(N1, N2, 7)
+    R = Xr.sum(axis=1)      # N1 x 7
+    K = Xr.sum(axis=0)      # N2 x 7
+    nb = (R[:, None, :] + K[None, :, :] - 2.0 * Xr).reshape(N1 * N2, 7)
+    deg = N1 + N2 - 2
+    want = nb / deg if deg else np.zeros_like(nb)
+    assert np.allclose(O.mean_aggregate(g, X), want, rtol=0, atol=1e-12)
+    assert np.allclose(O.mean_aggregate_adjoint(g, X), want, rtol=0, atol=1e-12)
