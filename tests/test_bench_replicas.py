@@ -49,3 +49,20 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.replica_throughput(1, 10.0, 2.0) == 5.0
+
+
+def test_roofline_byte_counts():
+    """The loss kernel's algorithmic and compulsory bytes at the default
+    workload (N = 10^6, nnz = 5*10^6, S = 256, BF16 G), from their parts."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    N, nnz, S = 10**6, 5 * 10**6, 256
+    gather = nnz * S * 4            # every neighbour row of P, FP32
+    own = N * S * 4                 # each row's own P row
+    g_out = N * S * 2               # G_Z2 in BF16
+    csr = 4 * (N + 1) + 4 * nnz
+    bits = N * (S // 32) * 4
+    assert bench.loss_kernel_bytes(N, nnz, S, 2) == gather + own + g_out + csr + bits == 6_712_000_004
+    assert bench.loss_compulsory_bytes(N, nnz, S, 2) == own + g_out + csr + bits
+    assert bench.loss_kernel_bytes(N, nnz, S, 4) - bench.loss_kernel_bytes(N, nnz, S, 2) == N * S * 2
