@@ -198,3 +198,19 @@ def test_constraint_graph_aggregation_by_line_sums(N1, N2):
     want = nb / deg if deg else np.zeros_like(nb)
     assert np.allclose(O.mean_aggregate(g, X), want, rtol=0, atol=1e-12)
     assert np.allclose(O.mean_aggregate_adjoint(g, X), want, rtol=0, atol=1e-12)
+
+
+def test_early_stop_monitors_the_dbm_penalty_unweighted():
+    """For DBM the monitored loss is sum_s (cost_s + pen_s): the penalty term
+    already carries its lambdas, so the per-shot lambda vector is not applied."""
+    S = 3
+    seq = []
+    for t in range(6):
+        cost = np.full(S, -1.0 - 0.5 * t)     # falls by 0.5 per shot and step
+        pen = np.full(S, 2.0 + 0.25 * t)      # rises by 0.25
+        seq.append((cost, pen, np.zeros(S)))
+    lam = np.full(S, 7.0)
+    # unweighted, cost + pen falls by 0.25 per shot and step: never stale
+    assert O.early_stop_step(seq, [1.0] * 6, lam, O.DBM, 1e-9, 3) == -1
+    # weighted by lambda = 7 it would rise by 1.25 (stale from step 1 on)
+    assert O.early_stop_step(seq, [1.0] * 6, lam, O.MIS, 1e-9, 3) == 3
