@@ -239,3 +239,24 @@ def test_step_at_the_papers_width_matches_oracle():
     ev = O.integer_eval(g, x, np.ones(S), O.DBM, inst=inst)
     assert np.array_equal(rec["violations"], ev["violations"])
     assert np.allclose(rec["qubo"], ev["qubo"], rtol=1e-12, atol=1e-9)
+
+
+def test_device_early_stop_matches_oracle_rule():
+    """The device monitor on a DBM context (lambda vector of ones, the
+    penalty carrying its own lambdas) stops where the oracle's rule does on
+    the same per-step terms."""
+    N1, N2, S, T = 8, 6, 12, 200
+    rp, col = I.dbm_graph(N1, N2)
+    C, M, lam4, pq, _ = _mixed_shots(N1, N2, S, seed=5)
+    s = cpra.Solver(rp, col, problem=cpra.DBM, S=S, H0=16, H1=16, lr=1e-3, gamma0=-2.0,
+                    gamma1=0.1, schedule_steps=T, es_tol=1e-2, es_patience=4, seed=3)
+    s.set_dbm(N1, C, M, lam4, pq)
+    seq, gammas = [], []
+    for t in range(60):
+        terms = s.step(t, want_terms=True).astype(np.float32)
+        seq.append((terms[:S], terms[S:2 * S], terms[2 * S:3 * S]))
+        gammas.append(float(np.float32(O.gamma_schedule(t, T, -2.0, float(np.float32(0.1))))))
+    got = s.early_stop_step()
+    s.close()
+    want = O.early_stop_step(seq, gammas, np.full(S, 7.0), O.DBM, float(np.float32(1e-2)), 4)
+    assert got == want
