@@ -230,7 +230,10 @@ STEP_CASES = [
 ]
 
 
-def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None):
+def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None, plain=False):
+    """One GPU step from seeded state and the oracle's step from the same
+    state.  With plain=True the BF16 form is also compared with the oracle
+    that decides the ReLU signs on FP64 Z1 (out["ref_plain"])."""
     problem, div, alpha, nu, S, H, N, gk = case
     rp, col = graph_of(gk, N, seed=N + S)
     g = O.Graph(rp, col)
@@ -266,32 +269,44 @@ def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=No
         # the library keeps the offset in the dense layers' dtype
         cfg["init_logits"] = (O.bf16_round(init_logits) if precision == cpra.BF16
                               else np.asarray(init_logits, dtype=np.float64))
-    ref = O.step(g, theta, X0, cfg, t=t_prev + 1,
-                 adam_state=dict(m_theta=mt, v_theta=vt, m_X0=mx.reshape(N, H),
-                                 v_X0=vx.reshape(N, H)))
+    adam_state = dict(m_theta=mt, v_theta=vt, m_X0=mx.reshape(N, H), v_X0=vx.reshape(N, H))
+    ref = O.step(g, theta, X0, cfg, t=t_prev + 1, adam_state=adam_state)
+    if plain:
+        cfg_plain = dict(cfg)
+        cfg_plain.pop("relu_decision", None)
+        out["ref_plain"] = O.step(g, theta, X0, cfg_plain, t=t_prev + 1, adam_state=adam_state)
     return out, ref, g, lam, gamma, theta, X0
 
 
-def _check_step(out, ref, g, lam, gamma, theta, X0, S, H, tol, problem):
-    assert np.abs(out["P"] - ref["P"]).max() <= tol
+def _step_errors(out, ref, lam, gamma, S, H, problem):
+    """The parity measures of one step against one oracle result: max |dP|,
+    the per-shot loss error over the cancellation-safe normaliser, Psi
+    relative to |Psi|, and the norm-wise relative error of each parameter
+    gradient block and of the embedding gradient."""
+    e = {"P": float(np.abs(out["P"] - ref["P"]).max())}
     t = out["terms"]
     lam64 = lam.astype(np.float64) if problem == O.MIS else np.zeros(S)
     rt = ref["terms"]
     norm = np.abs(rt["cost"]) + lam64 * np.abs(rt["pen"]) + abs(gamma) * rt["ann"]
     Lg = t[:S] + lam64 * t[S:2 * S] + gamma * t[2 * S:3 * S]
     Lr = rt["cost"] + lam64 * rt["pen"] + gamma * rt["ann"]
-    assert np.max(np.abs(Lg - Lr) / norm) <= tol
-    if rt["psi"] != 0:
-        assert abs(t[3 * S] - rt["psi"]) <= tol * abs(rt["psi"])
+    e["loss"] = float(np.max(np.abs(Lg - Lr) / norm))
+    e["psi"] = float(abs(t[3 * S] - rt["psi"]) / abs(rt["psi"])) if rt["psi"] != 0 else 0.0
     lay = I.param_layout(H, H, S)
     for name in ("Wcat1", "b1", "Wcat2", "b2"):
         off, shape = lay[name]
         n = int(np.prod(shape))
         a, b = out["grad"][off:off + n], ref["grads"]["theta"][off:off + n]
-        e = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert e <= tol, (name, e)
-    e = np.linalg.norm(out["gX0"].reshape(X0.shape) - ref["grads"]["X0"]) / np.linalg.norm(ref["grads"]["X0"])
-    assert e <= tol, ("X0", e)
+        e[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    gX = ref["grads"]["X0"]
+    e["X0"] = float(np.linalg.norm(out["gX0"].reshape(gX.shape) - gX) / np.linalg.norm(gX))
+    return e
+
+
+def _check_step(out, ref, g, lam, gamma, theta, X0, S, H, tol, problem):
+    e = _step_errors(out, ref, lam, gamma, S, H, problem)
+    for k, v in e.items():
+        assert v <= tol, (k, v)
     # Adam: the step taken equals Adam (FP64) applied to the step's own
     # gradients, which the checks above hold to the oracle's
     mt, vt, mx, vx, tt = out["adam0"]
@@ -325,10 +340,40 @@ def test_full_step_fp32_matches_oracle(case):
         assert out["ham"] == ev["pair_hamming"]
 
 
+# Quantities that the layer-1 ReLU decisions cannot move by more than the
+# rounding of the values they gate: H1 = max(Z1, 0) is continuous where a
+# sign flips, so P, the loss terms and the layer-2 gradients (dWcat2 =
+# G_Z2^T [H1 | M2]) stay close to FP64 whichever precision decides the sign.
+# The layer-1 and embedding gradients carry G_Z1 = G_H1 * 1[Z1 > 0], which a
+# flipped sign changes by a whole G_H1 entry.
+MASK_CONTINUOUS = ("P", "loss", "psi", "Wcat2", "b2")
+
+
+def _report_plain(name, case, e_matched, e_plain):
+    """Appends one JSON line per case to $CPRA_PARITY_REPORT (if set): the
+    BF16 form's parity measures against the decision-matched and the plain
+    FP64 oracle."""
+    import json
+    import os
+    path = os.environ.get("CPRA_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": name, "case": [str(c) for c in case],
+                                "vs_matched_fp64": e_matched, "vs_plain_fp64": e_plain}) + "\n")
+
+
 @pytest.mark.parametrize("case", STEP_CASES)
 def test_full_step_bf16_matches_oracle(case):
-    out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, cpra.BF16)
+    out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, cpra.BF16, plain=True)
     _check_step(out, ref, g, lam, gamma, theta, X0, case[4], case[5], 2e-2, case[0])
+    # against the plain FP64 oracle (every ReLU sign decided on FP64 Z1): the
+    # mask-continuous results meet the same 2e-2 bar; the layer-1 gradients
+    # are reported
+    e_m = _step_errors(out, ref, lam, gamma, case[4], case[5], case[0])
+    e_p = _step_errors(out, out["ref_plain"], lam, gamma, case[4], case[5], case[0])
+    _report_plain("full_step_bf16", case, e_m, e_p)
+    for k in MASK_CONTINUOUS:
+        assert e_p[k] <= 2e-2, (k, e_p[k])
 
 
 @pytest.mark.parametrize("precision", [cpra.FP32, cpra.BF16])

@@ -62,6 +62,34 @@ def test_train_step_matches_oracle(precision, tol, shape):
     step = np.linalg.norm(th_ref - theta)
     assert np.linalg.norm(net.params(0) - th_ref) <= 10 * tol * step
     net.close()
+    if precision == cpra.BF16:
+        # against the plain FP64 oracle (ReLU signs decided on FP64 values):
+        # the logits, the loss and the last layer's gradient are continuous
+        # where a sign flips and meet the same bar; the gradients of the
+        # two ReLU layers are reported
+        cp = WO.forward(g, theta, X, F, H, S)
+        gp = WO.backward(g, theta, cp, Y, F, H, S)
+        e_p = {"Z3": float(np.abs(logits - cp["Z3"]).max() / np.abs(cp["Z3"]).max()),
+               "loss": float(abs(loss - WO.bce(cp["Z3"], Y)) / WO.bce(cp["Z3"], Y))}
+        o = 0
+        for name, n in (("W1", 2 * H * F), ("b1", H), ("W2", 2 * H * H), ("b2", H),
+                        ("W3", 2 * S * H), ("b3", S)):
+            e_p[name] = float(np.linalg.norm(grad[o:o + n] - gp[o:o + n]) / np.linalg.norm(gp[o:o + n]))
+            o += n
+        _report_plain(shape, e_p)
+        for k in ("Z3", "loss", "W3", "b3"):
+            assert e_p[k] <= tol, (k, e_p[k])
+
+
+def _report_plain(shape, e_plain):
+    """One JSON line per case to $CPRA_PARITY_REPORT (if set)."""
+    import json
+    import os
+    path = os.environ.get("CPRA_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": "warm_train_step_bf16", "case": list(shape),
+                                "vs_plain_fp64": e_plain}) + "\n")
 
 
 def test_device_features():
