@@ -93,11 +93,13 @@ def read_peaks():
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    """Per-launch DRAM bytes of `kernel` at `workload` from its committed ncu
+    summary, if that was taken on the current kernel source; else None.
+    Returns (bytes, basis): the summary's DRAM capture is taken on a smaller
+    case of the same kernel and scaled by the units (node rows) processed."""
     p = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
     if not os.path.exists(p):
-        return None
+        return None, None
     fields = {}
     for line in open(p):
         if ":" in line and line.startswith("- "):
@@ -105,14 +107,14 @@ def ncu_traffic(kernel: str, workload: str):
             fields[k.strip()] = v.strip().strip("`")
     src = os.path.join(ROOT, "paper_2402_02190_gb300", "csrc", fields.get("source", "k_loss.cu"))
     if not os.path.exists(src):
-        return None
+        return None, None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if fields.get("source_sha256_16") != sha:
-        return None
+        return None, None
     try:
-        return float(fields["dram_bytes_per_launch"])
+        return float(fields["dram_bytes_per_launch"]), fields.get("traffic_basis")
     except (KeyError, ValueError):
-        return None
+        return None, None
 
 
 def max_over_ranks(x: float, dist_mod=None, device="cuda") -> float:
@@ -342,6 +344,29 @@ def run_gpu(args):
     h2d = (8 * (N + 1) + 4 * nnz + (4 * S if lam is not None else 0)) / args.steps
     d2h = (3 * S + 1) * 4 + (S * 24 + 8) / args.steps
 
+    # the plain FP32 form (every dense layer in FP32) on the same graph and
+    # shots, timed the same way: the comparator of the BF16 form
+    fp32_form = None
+    if w["precision"] == 1 and not args.no_fp32_form:
+        s3 = cpra.Solver(rp, col, lam=lam, **dict(kw, precision=0))
+        for t in range(args.warmup):
+            s3.step(t)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(s3.stream)
+        for t in range(args.warmup, args.warmup + args.steps):
+            s3.step(t)
+        e1.record(s3.stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks(e0.elapsed_time(e1), dist)
+        s3.close()
+        fp32_form = {"ms_per_step": ms32 / args.steps,
+                     "value": replica_throughput(world, nnz * S * args.steps, ms32 / 1e3),
+                     "unit": METRIC, "steps": args.steps, "warmup": args.warmup,
+                     "how": "the same workload with precision fp32 (all dense layers fp32), "
+                            "per-step launches, CUDA events on the library stream"}
+
     value = replica_throughput(world, nnz * S * args.steps, ms / 1e3)
     peak, peak_src = read_peaks()
     loss_ms, loss_n = prof.get("loss_fused", (0.0, 0))
@@ -349,7 +374,7 @@ def run_gpu(args):
     alg = loss_kernel_bytes(N, nnz, S, g_bytes)
     comp = loss_compulsory_bytes(N, nnz, S, g_bytes)
     achieved = alg / (loss_ms / loss_n / 1e3) / 1e9 if loss_n else None
-    traffic = ncu_traffic("loss_fused", args.workload)
+    traffic, traffic_basis = ncu_traffic("loss_fused", args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -368,6 +393,7 @@ def run_gpu(args):
         "roofline": {"kernel": "loss_fused", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_basis": traffic_basis,
                      "alg_bytes_per_launch": alg, "avg_ms": loss_ms / loss_n if loss_n else None,
                      # a second line: the bound if no neighbour row were re-read
                      # (the gathers' amplification over it is alg / compulsory)
@@ -380,6 +406,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "seconds": e2e_s},
         "gpu_launches": launches,
+        "fp32_form": fp32_form,
         "graph": None if graph_ms is None else {
             "ms_per_step": graph_ms / args.steps,
             "value": replica_throughput(world, nnz * S * args.steps, graph_ms / 1e3),
@@ -429,30 +456,55 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ quality mode
+def _reach(trace, target):
+    from paper_2402_02190_gb300 import warm as WM
+    r = WM.time_to_reach(trace, target)
+    return {"seconds_to_99pct": r[0] if r else None, "steps_to_99pct": r[1] if r else None,
+            "best": trace[-1][2], "total_seconds": trace[-1][0]}
+
+
 def run_quality(args):
     """The metric's second half: wall time for the BF16 + warm-start form to
     come within 1% of the best MIS the plain FP32 form finds on the same graph
-    (the workload's graph, shots and widths), plus the warm-start network's
-    training summary and a held-out comparison (objective gap, steps saved)."""
+    (the workload's graph, shots and widths).
+
+    Arms on that graph, all from the same seeds: plain FP32 and plain BF16
+    with the full schedule (gamma -2 -> 0.1), plain BF16 and BF16 + warm start
+    with the warm arm's shorter convex phase (gamma from q_warm_gamma0), and
+    BF16 + warm start with the full schedule.  The warm start's own effect is
+    the warm arm against the plain arm with the same schedule.  Also: the
+    warm-start network's training cost (target solves + fit) and how many
+    solves it takes to pay for it, and a held-out check where every graph's
+    warm and schedule-matched plain runs are measured against a longer plain
+    run (q_ref_steps, full schedule) whose final binarisation is reported."""
     import torch
     from paper_2402_02190_gb300 import cpra
     from paper_2402_02190_gb300 import warm as WM
     w = WORKLOADS[args.workload]
-    S, H, lam_spec = w["S"], w["H"], w["lam"]
+    S, H = w["S"], w["H"]
     lam = make_lambda(w)
     q = args.q_steps
+    g0 = args.q_warm_gamma0
     out = {"metric": "wall time to within 1% of the FP32 form's best MIS (BF16 + warm start)",
-           "unit": "s", "higher_is_better": False, "mode": "quality", "data": "synthetic",
+           "unit": "s", "higher_is_better": False, "mode": "quality",
+           "data": "synthetic (seeded random regular graphs)",
            "config": {"workload": args.workload, "steps": q, "eval_every": args.q_eval,
-                      "warm_graphs": args.q_train, "warm_heldout": args.q_heldout}}
-    # 1. targets from plain CPRA on seeded training graphs (BF16)
+                      "warm_gamma0": g0, "warm_graphs": args.q_train,
+                      "warm_heldout": args.q_heldout, "graph_nodes": [args.q_nmin, args.q_nmax],
+                      "target_steps": args.q_target_steps, "heldout_ref_steps": args.q_ref_steps}}
+    # 1. targets from plain CPRA (BF16, full schedule) on seeded training graphs
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    graphs = WM.training_graphs(args.q_train + args.q_heldout, seed=77, n_min=1000, n_max=5000)
+    graphs = WM.training_graphs(args.q_train + args.q_heldout, seed=77, n_min=args.q_nmin,
+                                n_max=args.q_nmax)
+    t_gen = time.perf_counter() - t0
     train, held = graphs[:args.q_train], graphs[args.q_train:]
+    t0 = time.perf_counter()
     dataset = []
     for k, (rp, col, d) in enumerate(train):
         bits, _ = WM.cpra_targets(rp, col, S, lam, args.q_target_steps, cpra.BF16, H=64, seed=k + 1)
         dataset.append((rp, col, bits, 1000 + k))
+    torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     # 2. fit the warm-start network
     max_n = max(len(g[0]) - 1 for g in train) * args.q_batch
@@ -460,35 +512,68 @@ def run_quality(args):
     net = cpra.WarmStartNet(max_n, max_e, F=16, H=64, S=S, precision=cpra.BF16, lr=3e-3)
     t0 = time.perf_counter()
     losses = WM.train_network(net, dataset, args.q_epochs, args.q_batch)
+    torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     theta = net.params(0)
+    net.close()
     out["warm_training"] = {"graphs": len(dataset), "target_steps": args.q_target_steps,
+                            "graph_generation_seconds": t_gen,
                             "target_seconds": t_targets, "fit_seconds": t_fit,
+                            "cost_seconds": t_targets + t_fit,
                             "epochs": args.q_epochs, "loss_first": losses[0], "loss_last": losses[-1]}
-    # 3. held-out graphs: plain BF16 from random init vs BF16 + warm start
-    gaps, saved, reached = [], [], 0
+    # 3. held-out graphs: warm and schedule-matched plain runs against a long
+    #    plain run of the full schedule
+    per_graph = []
     for k, (rp, col, d) in enumerate(held):
-        big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
+        N = len(rp) - 1
+        big = cpra.WarmStartNet(N, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
         big.set_params(theta)
         L0 = WM.predict_logits(big, rp, col, 5000 + k)
-        plain = WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16, H=64, seed=7)
-        warm = WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16, H=64, seed=7,
-                            init_logits=L0, gamma0=args.q_warm_gamma0)
         big.close()
-        best = plain[-1][2]
-        gaps.append((warm[-1][2] - best) / max(best, 1))
-        tp = WM.time_to_reach(plain, 0.99 * best)
-        tw = WM.time_to_reach(warm, 0.99 * best)
-        if tw is not None:
-            reached += 1
-            saved.append(tp[1] - tw[1])
-    out["heldout"] = {"graphs": len(held), "mean_relative_gap_final": float(np.mean(gaps)),
-                      "reached_99pct": reached,
-                      "mean_steps_saved_to_99pct": float(np.mean(saved)) if saved else None}
-    # 4. the workload graph: FP32 plain vs BF16 + warm start, wall clock
+        fin = []
+        ref = WM.run_trace(rp, col, S, lam, args.q_ref_steps, args.q_eval, cpra.BF16, H=64, seed=7,
+                           final_terms=fin)
+        best = ref[-1][2]
+        arms = {
+            "plain_matched": WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval,
+                                          cpra.BF16, H=64, seed=7, gamma0=g0),
+            "warm": WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16,
+                                 H=64, seed=7, init_logits=L0, gamma0=g0),
+        }
+        row = {"N": N, "d": d, "ref_best": best,
+               "ref_binarised": WM.binarised_fraction(fin[0], N, S),
+               "ref_steps_to_99pct": (WM.time_to_reach(ref, 0.99 * best) or (None, None))[1]}
+        for name, tr in arms.items():
+            r = WM.time_to_reach(tr, 0.99 * best)
+            row[name] = {"best": tr[-1][2], "gap": (best - tr[-1][2]) / max(best, 1),
+                         "steps_to_99pct": r[1] if r else None}
+        per_graph.append(row)
+    def _mean(xs):
+        xs = [x for x in xs if x is not None]
+        return float(np.mean(xs)) if xs else None
+    out["heldout"] = {
+        "graphs": len(per_graph),
+        "ref_binarised_min": min(r["ref_binarised"] for r in per_graph),
+        "ref_binarised_mean": _mean([r["ref_binarised"] for r in per_graph]),
+        "warm_gap_mean": _mean([r["warm"]["gap"] for r in per_graph]),
+        "plain_matched_gap_mean": _mean([r["plain_matched"]["gap"] for r in per_graph]),
+        "warm_better_than_plain_matched": sum(r["warm"]["best"] > r["plain_matched"]["best"]
+                                              for r in per_graph),
+        "warm_worse_than_plain_matched": sum(r["warm"]["best"] < r["plain_matched"]["best"]
+                                             for r in per_graph),
+        "warm_reached_99pct": sum(r["warm"]["steps_to_99pct"] is not None for r in per_graph),
+        "plain_matched_reached_99pct": sum(r["plain_matched"]["steps_to_99pct"] is not None
+                                           for r in per_graph),
+        "warm_steps_to_99pct_mean": _mean([r["warm"]["steps_to_99pct"] for r in per_graph]),
+        "plain_matched_steps_to_99pct_mean": _mean([r["plain_matched"]["steps_to_99pct"]
+                                                    for r in per_graph]),
+        "per_graph": per_graph,
+    }
+    # 4. the workload graph: every arm, wall clock from context creation
     rp, col = make_graph(w)
     fp32 = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.FP32, H=H, seed=1)
     best = fp32[-1][2]
+    target = 0.99 * best
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
@@ -497,28 +582,35 @@ def run_quality(args):
     torch.cuda.synchronize()
     t_inf = time.perf_counter() - t0
     warm = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1, init_logits=L0,
-                        gamma0=args.q_warm_gamma0, t0=t0)
+                        gamma0=g0, t0=t0)
     big.close()
     plain16 = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1)
-    # the warm start under the full annealing schedule (gamma from -2)
-    warm_full = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1, init_logits=L0,
-                             gamma0=-2.0)
-    target = 0.99 * best
-    r32, rw, r16, rwf = (WM.time_to_reach(x, target) for x in (fp32, warm, plain16, warm_full))
-    out["traces"] = {k: [(round(a, 4), b, c) for a, b, c in x[::max(1, len(x) // 10)]]
-                     for k, x in (("fp32", fp32), ("bf16_warm", warm), ("bf16_plain", plain16))}
-    out["fp32"] = {"best": best, "seconds_to_99pct": r32[0] if r32 else None,
-                   "steps_to_99pct": r32[1] if r32 else None, "total_seconds": fp32[-1][0]}
-    out["bf16_warm"] = {"best": warm[-1][2], "seconds_to_99pct": rw[0] if rw else None,
-                        "steps_to_99pct": rw[1] if rw else None, "total_seconds": warm[-1][0],
-                        "warm_inference_seconds": t_inf}
-    out["bf16_plain"] = {"best": plain16[-1][2], "seconds_to_99pct": r16[0] if r16 else None,
-                         "steps_to_99pct": r16[1] if r16 else None, "total_seconds": plain16[-1][0]}
-    out["bf16_warm_full_schedule"] = {"best": warm_full[-1][2],
-                                      "seconds_to_99pct": rwf[0] if rwf else None,
-                                      "steps_to_99pct": rwf[1] if rwf else None}
-    out["value"] = rw[0] if rw else None
-    out["vs_fp32_seconds"] = r32[0] if r32 else None
+    plain16_m = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1, gamma0=g0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
+    big.set_params(theta)
+    L0 = WM.predict_logits(big, rp, col, 99)
+    warm_full = WM.run_trace(rp, col, S, lam, q, args.q_eval, cpra.BF16, H=H, seed=1,
+                             init_logits=L0, gamma0=-2.0, t0=t0)
+    big.close()
+    arms = {"fp32": fp32, "bf16_plain": plain16, "bf16_plain_matched_schedule": plain16_m,
+            "bf16_warm": warm, "bf16_warm_full_schedule": warm_full}
+    out["race"] = {"target": target, "fp32_best": best,
+                   "warm_inference_seconds": t_inf,
+                   "arms": {k: _reach(x, target) for k, x in arms.items()},
+                   "traces": {k: [(round(a, 4), b, c) for a, b, c in x[::max(1, len(x) // 10)]]
+                              for k, x in arms.items()}}
+    a = out["race"]["arms"]
+    rw, rm = a["bf16_warm"]["seconds_to_99pct"], a["bf16_plain_matched_schedule"]["seconds_to_99pct"]
+    saved = (rm - rw) if (rw is not None and rm is not None) else None
+    out["warm_effect"] = {
+        "vs": "bf16_plain_matched_schedule (same precision, same gamma schedule, same seed)",
+        "seconds_saved_per_solve": saved,
+        "training_cost_seconds": t_targets + t_fit,
+        "solves_to_amortise": ((t_targets + t_fit) / saved) if saved and saved > 0 else None}
+    out["value"] = rw
+    out["vs_fp32_seconds"] = a["fp32"]["seconds_to_99pct"]
     print(json.dumps(out))
 
 
@@ -623,6 +715,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip timing the FP32 form of a BF16 workload")
     ap.add_argument("--recompute", type=int, choices=[0, 1], default=None,
                     help="override the workload's activation-recompute setting")
     ap.add_argument("--graph", action="store_true",
@@ -632,8 +726,11 @@ def main():
                     help="time-to-quality run: FP32 plain vs BF16 + warm start on the workload graph")
     ap.add_argument("--q-steps", type=int, default=2000)
     ap.add_argument("--q-eval", type=int, default=50)
-    ap.add_argument("--q-train", type=int, default=96)
-    ap.add_argument("--q-heldout", type=int, default=8)
+    ap.add_argument("--q-train", type=int, default=512)
+    ap.add_argument("--q-heldout", type=int, default=64)
+    ap.add_argument("--q-nmin", type=int, default=1000)
+    ap.add_argument("--q-nmax", type=int, default=10000)
+    ap.add_argument("--q-ref-steps", type=int, default=3000)
     ap.add_argument("--q-target-steps", type=int, default=1000)
     ap.add_argument("--q-epochs", type=int, default=40)
     ap.add_argument("--q-batch", type=int, default=8)

@@ -99,10 +99,12 @@ def best_feasible(rec, problem=cpra.MIS) -> int:
 
 def run_trace(rp, col, S: int, lam, steps: int, eval_every: int, precision: int,
               init_logits=None, gamma0: float = -2.0, gamma1: float = 0.1, H: int = 64,
-              seed: int = 1, problem: int = cpra.MIS, t0=None):
+              seed: int = 1, problem: int = cpra.MIS, t0=None, final_terms=None):
     """A CPRA run that records (wall seconds since t0, step, running best
     feasible objective) at every evaluation.  Context creation and the
-    warm-start offset upload are inside the timed span."""
+    warm-start offset upload are inside the timed span.  If `final_terms`
+    is a list, the last step's loss terms (cost_s, pen_s, ann_s per shot,
+    then Psi) are appended to it."""
     import torch
     if t0 is None:
         torch.cuda.synchronize()
@@ -115,7 +117,9 @@ def run_trace(rp, col, S: int, lam, steps: int, eval_every: int, precision: int,
     trace = []
     best = -1
     for t in range(steps):
-        s.step(t)
+        terms = s.step(t, want_terms=final_terms is not None and t == steps - 1)
+        if terms is not None and final_terms is not None:
+            final_terms.append(terms)
         if (t + 1) % eval_every == 0 or t == steps - 1:
             rec, _, _ = s.round_eval()
             best = max(best, best_feasible(rec, problem))
@@ -130,3 +134,11 @@ def time_to_reach(trace, target):
         if best >= target:
             return sec, step
     return None
+
+
+def binarised_fraction(terms, N: int, S: int) -> float:
+    """How far a run has binarised, from its annealing terms: 1 minus the mean
+    of 1 - (2P-1)^2 over all N x S entries (1 = every P at 0 or 1, 0 = every P
+    at 1/2).  terms: cpra_step's loss terms (ann_s at [2S, 3S))."""
+    ann = np.asarray(terms, dtype=np.float64)[2 * S:3 * S]
+    return float(1.0 - ann.sum() / (N * S))
