@@ -314,6 +314,17 @@ CPRA_API int32_t cpra_profile_read(cpra_ctx* ctx, double* ms_out, int64_t* launc
                           int32_t n_ids);
 CPRA_API const char* cpra_kernel_name(int32_t id);
 
+/* Fault-injection hook for tests of the failure paths (no counterpart in the
+   paper).  ORs `bits` into the context's device error word on the context
+   stream, exactly as a kernel does when one of its bounded waits gives up
+   (bit 1, value 2: CPRA_ETIMEOUT) or when a loss term is not finite (bit 0,
+   value 1: CPRA_ENUMERIC).  The next call that reads the word -- cpra_step
+   with loss_terms_out non-NULL, or cpra_solve at its next evaluation --
+   returns that status (CPRA_ETIMEOUT first if both bits are set) and clears
+   the word; the context stays usable.  No GPU fault is involved.  Errors:
+   CPRA_EINVAL (NULL ctx, bits outside 1..3), CPRA_ECUDA. */
+CPRA_API cpra_status cpra_inject_error_flag(cpra_ctx* ctx, int32_t bits);
+
 /* Message of the last error on ctx; with ctx == NULL, the message of the
    last failed cpra_init_graph on the calling thread. */
 CPRA_API const char* cpra_last_error(const cpra_ctx* ctx);
@@ -390,7 +401,11 @@ CPRA_API cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* row
  *     launching anything.  N is not limited.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream
- *     capture.
+ *     capture.  With CUDA's default lazy module loading that first call is
+ *     also when the device reserves the array, so a caller with a fixed
+ *     memory budget should make it at start-up, before it commits its own
+ *     pool; if the device has no room for the array then, the call returns
+ *     CPRA_ENOMEM.
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents; each call writes every partial row before reading
  *     it, so nothing needs clearing.  Calls that overlap on the GPU

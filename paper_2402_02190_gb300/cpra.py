@@ -34,7 +34,8 @@ ABI_FUNCTIONS = (
     "cpra_last_error", "cpra_status_string", "cpra_destroy", "cpra_op_loss_scratch_bytes",
     "cpra_op_loss", "cpra_op_round_eval_scratch_bytes", "cpra_op_round_eval",
     "cpra_op_loss_noalloc", "cpra_forward", "cpra_backward", "cpra_early_stop_step",
-    "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_set_dbm", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
+    "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_set_dbm",
+    "cpra_inject_error_flag", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
     "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
     "cpra_ws_set_params", "cpra_ws_destroy",
 )
@@ -110,6 +111,7 @@ def lib():
         "cpra_param_count": (i64, [vp]),
         "cpra_launch_count": (i64, [vp]),
         "cpra_early_stop_step": (i64, [vp]),
+        "cpra_inject_error_flag": (i32, [vp, i32]),
         "cpra_steps": (i32, [vp, i64, i64]),
         "cpra_set_node_weights": (i32, [vp, vp, i64, i32]),
         "cpra_set_dbm": (i32, [vp, i32, vp, vp, i64, vp, vp]),
@@ -335,6 +337,13 @@ def cpra_set_dbm(ctx, N1: int, C_rew, M, lam4, pq) -> None:
 
 def cpra_steps(ctx, t0: int, n: int) -> None:
     _check(lib().cpra_steps(ctx, int(t0), int(n)), ctx)
+
+
+def cpra_inject_error_flag(ctx, bits: int) -> None:
+    """Fault injection for tests: sets the context's device error word as a
+    kernel whose bounded wait gave up (bits=2) or that produced a non-finite
+    loss term (bits=1) would."""
+    _check(lib().cpra_inject_error_flag(ctx, int(bits)), ctx)
 
 
 def cpra_early_stop_step(ctx) -> int:

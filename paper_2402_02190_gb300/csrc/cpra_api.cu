@@ -1292,6 +1292,19 @@ int64_t cpra_early_stop_step(cpra_ctx* c) {
   return h.stopped ? (int64_t)h.stop_step : -1;
 }
 
+cpra_status cpra_inject_error_flag(cpra_ctx* c, int32_t bits) {
+  if (!c) return CPRA_EINVAL;
+  if (bits < 1 || bits > 3) return fail(c, CPRA_EINVAL, "cpra_inject_error_flag: bits must be 1..3");
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  flag |= bits;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->err_flag, &flag, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "error-flag injection");
+}
+
 void cpra_profile_enable(cpra_ctx* c, int on) {
   if (!c) return;
   if (on && c->prof_ring.empty()) {

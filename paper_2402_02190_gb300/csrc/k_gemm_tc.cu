@@ -1036,7 +1036,8 @@ int tc_wgrad_launch(const GemmArgs& g, int num_sms, size_t part_floats, float* d
   if (smem < 120 * 1024) smem = 120 * 1024;
   const int grid = tiles * p.splits;
   // one split into a destination with row stride Nc: no partials to add
-  const bool direct = p.splits == 1 && ldo == p.Nc;
+  // (the kernel's epilogue stores 16-byte vectors, so dst must be 16-byte aligned)
+  const bool direct = p.splits == 1 && ldo == p.Nc && reinterpret_cast<uintptr_t>(dst) % 16 == 0;
   if (direct) p.part = dst;
   tc_wgrad_kernel<<<grid, kThreads, smem, st>>>(ta, tb, p);
   if (direct) return 1;

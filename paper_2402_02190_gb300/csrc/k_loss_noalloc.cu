@@ -14,7 +14,9 @@
 //     strides over rows with at most kMaxBlocks blocks).
 //   * The first call on a device looks the array's device address up with
 //     cudaGetSymbolAddress (once per device, under a lock); make that first
-//     call before any stream capture.
+//     call before any stream capture.  Under lazy module loading that call
+//     is also when the device reserves the array; if it has no room, the
+//     call returns CPRA_ENOMEM.
 //   * All calls on a device share the one array and it keeps the contents
 //     of the last call.  Nothing in it needs clearing: every call writes
 //     each partial row it later reads.  Calls whose work overlaps on the GPU
@@ -76,7 +78,12 @@ extern "C" cpra_status cpra_op_loss_noalloc(int64_t N, int32_t S, const int32_t*
   if (alpha < 2 || alpha % 2 || diversity_kind < 0 || diversity_kind > 1) return CPRA_EINVAL;
   if (grad_kind != 0 && grad_kind != 1) return CPRA_EINVAL;
   void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return CPRA_ECUDA;
+  const cudaError_t se = scratch_address(&base);
+  if (se == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // the failed reservation is not sticky: clear it
+    return CPRA_ENOMEM;
+  }
+  if (se != cudaSuccess) return CPRA_ECUDA;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

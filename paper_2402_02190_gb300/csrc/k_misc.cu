@@ -166,8 +166,10 @@ void adam_launch(int64_t n, float* theta, float* m, float* v, const float* g, fl
 
 namespace {
 
-// Single thread: the sums run in a fixed order with explicit roundings (no
-// contraction into fused multiply-adds), so the decision is reproducible.
+// One block: every thread computes the per-shot monitored values (they do not
+// depend on one another); thread 0 then adds them in shot order with
+// explicit roundings (no contraction into fused multiply-adds), so the
+// decision is reproducible.
 __global__ void early_stop_kernel(const float* __restrict__ terms, const float* __restrict__ lambda,
                                   int S, float tol, int patience, float ann_below,
                                   const StepScalars* sc, EarlyStopState* st) {
