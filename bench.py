@@ -535,6 +535,8 @@ def run_quality(args):
                            final_terms=fin)
         best = ref[-1][2]
         arms = {
+            "plain_full": WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval,
+                                       cpra.BF16, H=64, seed=7),
             "plain_matched": WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval,
                                           cpra.BF16, H=64, seed=7, gamma0=g0),
             "warm": WM.run_trace(rp, col, S, lam, args.q_target_steps, args.q_eval, cpra.BF16,
@@ -557,6 +559,13 @@ def run_quality(args):
         "ref_binarised_mean": _mean([r["ref_binarised"] for r in per_graph]),
         "warm_gap_mean": _mean([r["warm"]["gap"] for r in per_graph]),
         "plain_matched_gap_mean": _mean([r["plain_matched"]["gap"] for r in per_graph]),
+        "plain_full_gap_mean": _mean([r["plain_full"]["gap"] for r in per_graph]),
+        "warm_better_than_plain_full": sum(r["warm"]["best"] > r["plain_full"]["best"]
+                                           for r in per_graph),
+        "warm_worse_than_plain_full": sum(r["warm"]["best"] < r["plain_full"]["best"]
+                                          for r in per_graph),
+        "plain_full_reached_99pct": sum(r["plain_full"]["steps_to_99pct"] is not None
+                                        for r in per_graph),
         "warm_better_than_plain_matched": sum(r["warm"]["best"] > r["plain_matched"]["best"]
                                               for r in per_graph),
         "warm_worse_than_plain_matched": sum(r["warm"]["best"] < r["plain_matched"]["best"]
@@ -604,11 +613,18 @@ def run_quality(args):
     a = out["race"]["arms"]
     rw, rm = a["bf16_warm"]["seconds_to_99pct"], a["bf16_plain_matched_schedule"]["seconds_to_99pct"]
     saved = (rm - rw) if (rw is not None and rm is not None) else None
+    rf = a["bf16_plain"]["seconds_to_99pct"]
+    saved_f = (rf - rw) if (rw is not None and rf is not None) else None
     out["warm_effect"] = {
         "vs": "bf16_plain_matched_schedule (same precision, same gamma schedule, same seed)",
         "seconds_saved_per_solve": saved,
+        "matched_reached_target": rm is not None,
+        "vs_fastest_plain": "bf16_plain (full schedule, the fastest plain BF16 arm)",
+        "seconds_saved_per_solve_vs_fastest_plain": saved_f,
         "training_cost_seconds": t_targets + t_fit,
-        "solves_to_amortise": ((t_targets + t_fit) / saved) if saved and saved > 0 else None}
+        "solves_to_amortise": ((t_targets + t_fit) / saved) if saved and saved > 0 else None,
+        "solves_to_amortise_vs_fastest_plain": ((t_targets + t_fit) / saved_f)
+        if saved_f and saved_f > 0 else None}
     out["value"] = rw
     out["vs_fp32_seconds"] = a["fp32"]["seconds_to_99pct"]
     print(json.dumps(out))
