@@ -62,6 +62,7 @@ enum { CPRA_MIS = 0, CPRA_MAXCUT = 1,                 /* Table objective-functio
                             node i*N2 + j is the pair variable x_ij; shot s has its
                             own instance (C, M, lambda_1..4, p, q) from cpra_set_dbm */
 enum { CPRA_FP32 = 0, CPRA_BF16 = 1 };                /* dense-layer arithmetic   */
+enum { CPRA_FP32_TENSOR = 0, CPRA_FP32_CUDA_CORES = 1 };  /* engine of the FP32 form */
 enum { CPRA_DIV_STD = 0, CPRA_DIV_VAR = 1 };          /* Psi form                 */
 
 /* Configuration.  cpra_config_default() fills every field. */
@@ -113,6 +114,15 @@ typedef struct cpra_config {
                                head [B2|W2], b2 trains (the fine-tuning stage of
                                the two-stage schedule); layer 1 and the
                                embeddings keep their values                    */
+  int32_t fp32_engine;      /* FP32 form only.  CPRA_FP32_TENSOR (default): the
+                               dense layers and input gradients run on the
+                               tensor cores with split-TF32 operands (each FP32
+                               value exactly as three TF32 parts; six products
+                               per pair, FP32 accumulation: FP32 accuracy);
+                               shapes the tensor-core kernel does not take, and
+                               the weight gradients, stay on CUDA cores.
+                               CPRA_FP32_CUDA_CORES: every dense product on
+                               CUDA cores.  Ignored by the BF16 form          */
 } cpra_config;
 
 /* Result of rounding one shot (App. C.2) and evaluating it exactly. */
@@ -135,7 +145,7 @@ typedef struct cpra_ctx cpra_ctx;
    recompute 0, train_embedding 1, keep_emb_grad 0, DIV_STD, nu = 0,
    gamma -2 -> 0.1 over 3000 steps, Adam lr 1e-3, betas (0.9, 0.999),
    eps 1e-8, wd 0, seed 1, no early stopping (es_patience 0, es_tol 1e-5,
-   es_ann_below 0), train_encoder 1. */
+   es_ann_below 0), train_encoder 1, fp32_engine CPRA_FP32_TENSOR. */
 CPRA_API void cpra_config_default(cpra_config* cfg);
 
 /* Number of trainable GNN parameters excluding node embeddings:

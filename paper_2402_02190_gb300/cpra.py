@@ -23,6 +23,7 @@ CPRA_OK, CPRA_EINVAL, CPRA_ENOMEM, CPRA_ECUDA, CPRA_ENUMERIC, CPRA_ETIMEOUT, CPR
 MIS, MAXCUT, WMIS, DBM = 0, 1, 2, 3
 FP32, BF16 = 0, 1
 DIV_STD, DIV_VAR = 0, 1
+FP32_TENSOR, FP32_CUDA_CORES = 0, 1
 (T_THETA, T_THETA_M, T_THETA_V, T_EMB, T_EMB_M, T_EMB_V, T_GRAD, T_EMB_GRAD, T_P, T_GZ2,
  T_STEP, T_TERMS) = range(12)
 
@@ -58,7 +59,7 @@ class Config(C.Structure):
         ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
         ("weight_decay", C.c_float), ("seed", C.c_uint64), ("mem_cap_bytes", C.c_uint64),
         ("es_tol", C.c_float), ("es_patience", C.c_int32), ("es_ann_below", C.c_float),
-        ("train_encoder", C.c_int32),
+        ("train_encoder", C.c_int32), ("fp32_engine", C.c_int32),
     ]
 
 

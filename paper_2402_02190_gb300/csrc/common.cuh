@@ -16,6 +16,24 @@ template <typename T> __device__ __forceinline__ T from_f(float x);
 template <> __device__ __forceinline__ float from_f<float>(float x) { return x; }
 template <> __device__ __forceinline__ bf16 from_f<bf16>(float x) { return __float2bfloat16_rn(x); }
 
+// x rounded to TF32 (10 mantissa bits, round to nearest, ties away from
+// zero), as an FP32 value whose low 13 mantissa bits are zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// x = hi + mid + lo exactly, each part a TF32 value: hi = tf32(x),
+// mid = tf32(x - hi), lo = x - hi - mid (both differences are exact in FP32;
+// lo has at most 2 significant bits left, so it is a TF32 value too).
+__device__ __forceinline__ void split3(float x, float& hi, float& mid, float& lo) {
+  hi = tf32_rna(x);
+  const float r = x - hi;
+  mid = tf32_rna(r);
+  lo = tf32_rna(r - mid);
+}
+
 // Number of T elements in one 16-byte vector.
 template <typename T> struct V16 { static constexpr int n = 16 / (int)sizeof(T); };
 

@@ -157,12 +157,19 @@ struct cpra_ctx {
   void* W1t = nullptr;
   void* W2s = nullptr;
   void* W2t = nullptr;
+  // FP32 form on the tensor cores: the weights' split-TF32 parts (hi, mid,
+  // lo), K-major in both orientations
+  float* W1p[3] = {nullptr, nullptr, nullptr};
+  float* W1tp[3] = {nullptr, nullptr, nullptr};
+  float* W2p[3] = {nullptr, nullptr, nullptr};
+  float* W2tp[3] = {nullptr, nullptr, nullptr};
 
   int64_t opt_steps = 0;
   int64_t launches = 0;
   bool have_eval = false;
   bool fwd_valid = false;  // a cpra_forward whose activations are still in place
   bool use_tc = false;
+  bool use_tc3 = false;  // FP32 form: split-TF32 tensor-core GEMMs
   std::string err;
 
   bool prof = false;
@@ -217,6 +224,8 @@ std::string validate_config(const cpra_config* cfg) {
   if ((cfg->problem == CPRA_MIS || cfg->problem == CPRA_WMIS) && cfg->lambda == nullptr)
     return "MIS needs lambda[S]";
   if (cfg->train_encoder != 0 && cfg->train_encoder != 1) return "train_encoder must be 0 or 1";
+  if (cfg->fp32_engine != CPRA_FP32_TENSOR && cfg->fp32_engine != CPRA_FP32_CUDA_CORES)
+    return "fp32_engine must be CPRA_FP32_TENSOR or CPRA_FP32_CUDA_CORES";
   if (!(cfg->es_ann_below >= 0.f) || !std::isfinite(cfg->es_ann_below))
     return "es_ann_below must be finite and >= 0";
   if (cfg->schedule_steps < 1) return "schedule_steps must be >= 1";
@@ -331,6 +340,15 @@ size_t carve(cpra_ctx* c, void* base) {
   c->W1t = cv.take<uint16_t>((size_t)c->H1 * 2 * c->H0);
   c->W2s = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
   c->W2t = cv.take<uint16_t>((size_t)c->S_pad * 2 * c->H1);
+  if (c->use_tc3) {
+    const size_t w1 = (size_t)c->H1 * 2 * c->H0, w2 = (size_t)c->S_pad * 2 * c->H1;
+    for (int k = 0; k < 3; ++k) {
+      c->W1p[k] = cv.take<float>(w1);
+      c->W1tp[k] = cv.take<float>(w1);
+      c->W2p[k] = cv.take<float>(w2);
+      c->W2tp[k] = cv.take<float>(w2);
+    }
+  }
   return cv.off + kAlign;
 }
 
@@ -343,6 +361,9 @@ void set_dims(cpra_ctx* c, int64_t N, int64_t nnz, const cpra_config* cfg) {
   c->H0 = cfg->H0;
   c->H1 = cfg->H1;
   c->act_dt = cfg->precision == CPRA_BF16 ? DT_BF16 : DT_F32;
+  // the split-TF32 engine of the FP32 form (its weight shadows are part of
+  // the workspace; tc_prepare at init may still turn it off)
+  c->use_tc3 = (c->act_dt == DT_F32) && cfg->fp32_engine == CPRA_FP32_TENSOR && tc_available();
   c->nparam = layout_of(cfg->H0, cfg->H1, cfg->S).total;
   c->recompute = cfg->recompute != 0;
   c->wmis = cfg->problem == CPRA_WMIS;
@@ -380,6 +401,10 @@ void refresh_shadows(cpra_ctx* c) {
   if (c->act_dt == DT_BF16) {
     weight_shadows_launch(c->theta, c->H0, c->H1, c->S, c->S_pad, c->W1s, c->W1t, c->W2s,
                           c->W2t, c->stream);
+    c->launches += 1;
+  } else if (c->use_tc3) {
+    weight_split_launch(c->theta, c->H0, c->H1, c->S, c->S_pad, c->W1p, c->W1tp, c->W2p, c->W2tp,
+                        c->stream);
     c->launches += 1;
   }
 }
@@ -424,12 +449,32 @@ char* act_off(void* base, int64_t elems, const cpra_ctx* c) {
 void dense(cpra_ctx* c, const GemmArgs& g0) {
   GemmArgs g = g0;
   g.err_flag = c->err_flag;
+  if (g.B_lo) {  // split-TF32 operands, accepted by tc3_gemm_supported at the call site
+    c->launches += tc3_gemm_launch(g, c->num_sms, c->stream);
+    return;
+  }
   if (c->use_tc && tc_gemm_supported(g)) {
     c->launches += tc_gemm_launch(g, c->num_sms, c->stream);
   } else {
     gemm_simt_launch(g, c->stream);
     c->launches += 1;
   }
+}
+
+// FP32 form: the same product with the weights' split-TF32 parts (hi, mid,
+// lo; K-major, row pitch ldb) when the tensor-core kernel takes this shape;
+// g keeps its CUDA-core form otherwise.
+void use_split_tf32(const cpra_ctx* c, GemmArgs& g, float* const* parts, int64_t K, int64_t ldb) {
+  if (!c->use_tc3) return;
+  GemmArgs t = g;
+  t.B = parts[0];
+  t.B_mid = parts[1];
+  t.B_lo = parts[2];
+  t.K = K;
+  t.ldb = ldb;
+  t.db = DT_F32;
+  t.b_kmajor = 1;
+  if (tc3_gemm_supported(t)) g = t;
 }
 
 // Weight gradient C[M x Nc] = A^T B over K = N rows, split-K with a fixed-
@@ -509,6 +554,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     // recompute: H1's block is overwritten by the backward, so its ReLU mask
     // (all the layer-1 adjoint needs of it) is kept as bits, 1/16 of H1
     if (c->recompute) { g.out1 = c->relu_bits; g.ld1 = H1 / 16; }
+    if (c->act_dt == DT_F32) use_split_tf32(c, g, c->W1p, 2 * H0, 2 * H0);
     dense(c, g);
   }
   {  // M2 = mean_agg(H1)
@@ -532,6 +578,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     g.epi = EPI_BIAS_SIGMOID; g.bias = c->theta + L.b2;
     g.out0 = c->P; g.ld0 = c->S_pad; g.d0 = DT_F32; g.n_valid = c->S;
     if (c->init_logits) { g.addend = c->init_logits; g.ld_add = c->S_pad; g.d_add = c->act_dt; }
+    if (c->act_dt == DT_F32) use_split_tf32(c, g, c->W2p, 2 * H1, 2 * H1);
     dense(c, g);
   }
   if (dbm && do_loss) {  // matching line sums R, K, T, U and the per-shot coefficients
@@ -624,6 +671,8 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
     g.out0 = c->GHM; g.ld0 = 2 * H1; g.d0 = c->act_dt;
     g.out1 = act_off(c->GHM, H1, c); g.ld1 = 2 * H1; g.d1 = c->act_dt;
     g.row_scale = c->inv_deg; g.n_valid = 2 * H1;
+    // (the split-TF32 form reads G_Z2 over its padded width: pad columns are 0)
+    if (!bf) use_split_tf32(c, g, c->W2tp, c->S_pad, c->S_pad);
     dense(c, g);
   }
   {  // G_Z1 = (G_H1a + sum_j G_M2_j/deg_j) * 1[H1 > 0], db1 = colsum(G_Z1)
@@ -660,6 +709,7 @@ cpra_status run_backward(cpra_ctx* c, bool emb_grad, bool fuse_adam = false) {
       g.out0 = c->GXM; g.ld0 = 2 * H0; g.d0 = c->act_dt;
       g.out1 = act_off(c->GXM, H0, c); g.ld1 = 2 * H0; g.d1 = c->act_dt;
       g.row_scale = c->inv_deg; g.n_valid = 2 * H0;
+      if (!bf) use_split_tf32(c, g, c->W1tp, H1, H1);
       dense(c, g);
     }
     {  // dX0 = G_X0a + sum_j G_M1_j/deg_j  [then Adam on h^0]
@@ -720,6 +770,10 @@ cpra_status check_err_flag(cpra_ctx* c) {
     cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream);
     return fail(c, CPRA_ETIMEOUT, "a bounded device-side wait gave up (tensor-core pipeline)");
   }
+  if (flag & 4) {
+    cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream);
+    return fail(c, CPRA_ECUDA, "a tensor-core GEMM could not be set up (its product is missing)");
+  }
   if (flag & 1) {
     cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream);
     return fail(c, CPRA_ENUMERIC, "non-finite loss term");
@@ -761,6 +815,7 @@ void cpra_config_default(cpra_config* cfg) {
   cfg->es_patience = 0;
   cfg->es_ann_below = 0.f;
   cfg->train_encoder = 1;
+  cfg->fp32_engine = CPRA_FP32_TENSOR;
 }
 
 int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S) {
@@ -878,14 +933,15 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   init_uniform_launch(c->theta + L.b2, c->S, 1.f / std::sqrt((float)c->H1), seed, 4, st);
   init_normal_launch(c->X0m, N * c->H0, seed, 5, st);
   c->launches += 5;
-  refresh_shadows(c);
-  refresh_emb_shadow(c);
-  if (c->use_tc) {
+  if (c->use_tc || c->use_tc3) {
     std::string tmsg;
     if (!tc_prepare(c->num_sms, &tmsg)) {
       c->use_tc = false;
+      c->use_tc3 = false;  // shadows stay carved, unused
     }
   }
+  refresh_shadows(c);
+  refresh_emb_shadow(c);
   s = cuda_check(c, cudaStreamSynchronize(st), "init");
   if (s == CPRA_OK) s = cuda_check(c, cudaGetLastError(), "init kernels");
   if (s != CPRA_OK) return bail(s);

@@ -275,6 +275,123 @@ __device__ __forceinline__ int epilogue16(const TcParams& p, int64_t row, int n,
   }
 }
 
+// The epilogue role: NW warps, NW/4 per TMEM lane quarter (a warp may read
+// the lanes of quarter warp & 3), `ew` this warp's index among them.  Per
+// tile: TMEM -> registers -> bias / activation / split -> shared-memory
+// staging -> TMA tensor store; the accumulator is handed back through
+// tempty.
+// Epilogue of 16 columns c .. c+15 (tile-relative; n0 + c < Nc) of one row
+// per lane (row0 = the warp's first row): bias / activation / split, then
+// either mask bits stored directly or a shared-memory staging buffer (two
+// per warp, alternating through sb) written out by a TMA tensor store.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const TcParams& p, const CUtensorMap* tmO0,
+                                               const CUtensorMap* tmO1, uint8_t* stg, int& sb,
+                                               int lane, int64_t row0, int n0, int c, float* v) {
+  const int64_t row = row0 + lane;
+  int col;
+  const int which = epilogue16<EPI>(p, row, n0 + c, v, &col);
+  if constexpr (EPI == EPI_BIAS_RELU) {
+    // optional ReLU mask of the stored activation (dtype d0) as bits
+    if (p.out1 && row < p.M) {
+      uint32_t bits = 0;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float h = v[i];
+        if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
+        bits |= (h > 0.f ? 1u : 0u) << i;
+      }
+      static_cast<uint16_t*>(p.out1)[row * p.ld1 + (n0 + c) / 16] = static_cast<uint16_t>(bits);
+    }
+  }
+  if constexpr (EPI == EPI_RELU_BITS) {
+    // mask of the activation as stored in dtype d0; no tile store
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float h = v[i];
+      if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
+      bits |= (h > 0.f ? 1u : 0u) << i;
+    }
+    if (row < p.M)
+      static_cast<uint16_t*>(p.out0)[row * p.ld0 + (n0 + c) / 16] = static_cast<uint16_t>(bits);
+    return;
+  }
+  uint8_t* buf = stg + sb * kStgBytes;
+  // the tensor store that last read this buffer must be done with it
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+  __syncwarp();
+  if ((which ? p.d1 : p.d0) == DT_BF16) stage_row_bf16(buf, lane, v);
+  else stage_row_f32(buf, lane, v);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {  // rows past M are clipped by the tensor map
+    tma_store_2d(which ? tmO1 : tmO0, buf, col, static_cast<int>(row0));
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+  sb ^= 1;
+}
+
+// The epilogue role: NW warps, NW/4 per TMEM lane quarter (a warp may read
+// the lanes of quarter warp & 3), `ew` this warp's index among them.  Per
+// tile: TMEM -> registers -> epilogue_chunk; the accumulator is handed back
+// through tempty.
+template <int EPI, int NW>
+__device__ __forceinline__ void epilogue_role(const TcParams& p, const CUtensorMap* tmO0,
+                                              const CUtensorMap* tmO1, uint8_t* Stg,
+                                              uint64_t* tfull, uint64_t* tempty,
+                                              volatile int* abort_flag, uint32_t tmem_base,
+                                              int warp, int ew, int lane, int group, int groups,
+                                              int n0) {
+  const int quarter = warp & 3;                 // TMEM lanes this warp may read
+  constexpr int parts = NW / 4;                 // column parts per lane quarter
+  const int cq = ew >> 2;
+  const int nch = p.BN / 16;                    // 16-column chunks, split between parts
+  const int c_begin = 16 * (nch * cq / parts);
+  const int c_end = 16 * (nch * (cq + 1) / parts);
+  uint8_t* stg = Stg + static_cast<size_t>(ew) * 2 * kStgBytes;
+  int sb = 0;
+  int it = 0;
+  for (int64_t mt = group; mt < p.m_tiles; mt += groups, ++it) {
+    const int acc = it & 1;
+    const uint32_t acc_par = (static_cast<uint32_t>(it) >> 1) & 1u;
+    if (!mbar_wait(tfull + acc, acc_par, abort_flag)) {
+      if (lane == 0) {
+        *abort_flag = 1;
+        if (p.err_flag) atomicOr(p.err_flag, 2);
+      }
+      break;
+    }
+    tc_fence_after();
+    const int64_t row0 = mt * kBM + quarter * 32;
+    const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                           static_cast<uint32_t>(acc * p.acc_stride);
+    for (int c2 = c_begin; c2 < c_end; c2 += 32) {
+      // two TMEM loads in flight per wait
+      uint32_t r[2][16];
+      const bool two = c2 + 16 < c_end;
+      tmem_ld16_issue(taddr + static_cast<uint32_t>(c2), r[0]);
+      if (two) tmem_ld16_issue(taddr + static_cast<uint32_t>(c2 + 16), r[1]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        const int c = c2 + 16 * h;
+        if (n0 + c >= p.Nc) continue;  // ragged last n tile: nothing stored past Nc
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
+        epilogue_chunk<EPI>(p, tmO0, tmO1, stg, sb, lane, row0, n0, c, v);
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(tempty + acc);
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -426,92 +543,306 @@ tc_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       }
     }
   } else {
-    // ---------------- epilogue ----------------
-    const int ew = warp - 2;
-    const int quarter = warp & 3;                 // TMEM lanes this warp may read
-    constexpr int parts = kEpiWarps / 4;          // column parts per lane quarter
-    const int cq = ew >> 2;
-    const int nch = p.BN / 16;                    // 16-column chunks, split between parts
-    const int c_begin = 16 * (nch * cq / parts);
-    const int c_end = 16 * (nch * (cq + 1) / parts);
-    uint8_t* stg = Stg + static_cast<size_t>(ew) * 2 * kStgBytes;
-    int sb = 0;
-    int it = 0;
-    for (int64_t mt = group; mt < p.m_tiles; mt += groups, ++it) {
-      const int acc = it & 1;
-      const uint32_t acc_par = (static_cast<uint32_t>(it) >> 1) & 1u;
-      if (!mbar_wait(tfull + acc, acc_par, abort_flag)) {
-        if (lane == 0) give_up();
-        break;
-      }
-      tc_fence_after();
-      const int64_t row0 = mt * kBM + quarter * 32;
-      const int64_t row = row0 + lane;
-      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                             static_cast<uint32_t>(acc * p.acc_stride);
-      for (int c2 = c_begin; c2 < c_end; c2 += 32) {
-        // two TMEM loads in flight per wait
-        uint32_t r[2][16];
-        const bool two = c2 + 16 < c_end;
-        tmem_ld16_issue(taddr + static_cast<uint32_t>(c2), r[0]);
-        if (two) tmem_ld16_issue(taddr + static_cast<uint32_t>(c2 + 16), r[1]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !two) break;
-          const int c = c2 + 16 * h;
-          if (n0 + c >= p.Nc) continue;  // ragged last n tile: nothing stored past Nc
-          float v[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[h][i]);
-          int col;
-          const int which = epilogue16<EPI>(p, row, n0 + c, v, &col);
-          if constexpr (EPI == EPI_BIAS_RELU) {
-            // optional ReLU mask of the stored activation (dtype d0) as bits
-            if (p.out1 && row < p.M) {
-              uint32_t bits = 0;
-#pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                float h = v[i];
-                if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
-                bits |= (h > 0.f ? 1u : 0u) << i;
-              }
-              static_cast<uint16_t*>(p.out1)[row * p.ld1 + (n0 + c) / 16] =
-                  static_cast<uint16_t>(bits);
-            }
+    epilogue_role<EPI, kEpiWarps>(p, &tmO0, &tmO1, Stg, tfull, tempty, abort_flag, tmem_base, warp,
+                                  warp - 2, lane, group, groups, n0);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------- FP32 form: split TF32
+// C[M x Nc] = A[M x K] B[Nc x K]^T for FP32 operands, to FP32 accuracy, on
+// the tensor cores (tcgen05.mma kind::tf32).  Every operand value x is
+// split exactly into three TF32 values, x = x_hi + x_mid + x_lo, with
+// x_hi = tf32(x), x_mid = tf32(x - x_hi), x_lo = x - x_hi - x_mid (round to
+// nearest; 11 + 11 significant bits cover 22 of FP32's 24, and the last 2
+// fit in x_lo).  Each k block sums the six products whose order of
+// magnitude is at least 2^-22 of |A||B| (hi.hi, hi.mid, mid.hi, hi.lo,
+// lo.hi, mid.mid; the three left out are below 2^-32) into fresh TMEM
+// accumulators -- hi.hi in one, the five smaller products in another --
+// and the accumulation warps add both block sums into FP32 registers with
+// round-to-nearest.  The tensor core's own accumulation is thus limited to
+// one 32-deep k block, and the large sum to four additions in it:
+// accumulating whole tiles in TMEM measured 10-30x less accurate than FP32
+// CUDA-core GEMMs whatever the split (two-way or three-way), which points
+// at the rounding of the tensor core's accumulator rather than at the
+// operands.  Two accumulator pairs alternate so the MMAs of block j+1
+// overlap the read-out of block j.  The
+// weights arrive split (K-major hi, mid and lo copies written with the
+// weight shadows); A arrives raw through TMA and two converter warps split
+// each stage in shared memory: hi in place, mid and lo beside it.  Roles
+// per CTA (one per SM):
+//   warp 0       TMA producer (A stage, B_hi, B_mid and B_lo blocks)
+//   warp 1       TMEM allocation + MMA issuer
+//   warps 2..3   converters (A -> A_hi, A_mid, A_lo)
+//   warps 4..11  accumulation and epilogue, two per TMEM lane quarter:
+//                each holds up to 64 columns of its 32 rows in registers
+// Stages: [A_hi | A_mid | A_lo | B_hi | B_mid | B_lo], 32 K elements (128
+// bytes per row) each, 128-byte swizzle; the split is element-wise, so the
+// parts keep the swizzled layout of A.  Bounded waits as in the BF16 kernel.
+constexpr int kBK3 = 32;            // FP32 K elements per stage (128 bytes)
+constexpr int kBN3 = 128;           // widest n tile
+constexpr int kConvWarps = 2;
+constexpr int kEpiWarps3 = 8;
+constexpr int kThreads3 = 64 + 32 * (kConvWarps + kEpiWarps3);
+constexpr int kStgTotal3 = kEpiWarps3 * 2 * kStgBytes;
+constexpr uint32_t kAStage3 = kBM * kBK3 * 4;  // 16 KB
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 12 warps: at most 3 per SM sub-partition, so up to 168 registers per thread
+template <int EPI>
+__global__ void __launch_bounds__(kThreads3, 1)
+tc3_gemm_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+                   const __grid_constant__ CUtensorMap tmBm,
+                   const __grid_constant__ CUtensorMap tmBl,
+                   const __grid_constant__ CUtensorMap tmO0,
+                   const __grid_constant__ CUtensorMap tmO1, const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t b_bytes = static_cast<uint32_t>(p.BN) * kBK3 * 4;
+  const uint32_t stage_bytes = 3 * kAStage3 + 3 * b_bytes;
+  uint8_t* St = smem;
+  uint8_t* Stg = St + static_cast<size_t>(p.stages) * stage_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Stg + kStgTotal3);
+  uint64_t* conv = full + p.stages;
+  uint64_t* empty = conv + p.stages;
+  uint64_t* tfull = empty + p.stages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x % p.n_tiles_n;
+  const int group = blockIdx.x / p.n_tiles_n;
+  const int groups = gridDim.x / p.n_tiles_n;
+  const int n0 = n_tile * p.BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(conv + s, kConvWarps);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(tfull + 0, 1);
+    mbar_init(tfull + 1, 1);
+    mbar_init(tempty + 0, kEpiWarps3);
+    mbar_init(tempty + 1, kEpiWarps3);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    if (p.err_flag) atomicOr(p.err_flag, 2);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBm)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBl)) : "memory");
+      const uint32_t tx = kAStage3 + 3 * b_bytes;  // A raw + B_hi + B_mid + B_lo
+      uint32_t armed = 0, last_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups) {
+        for (int kb = 0; kb < p.n_kb; ++kb) {
+          if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) {
+            give_up();
+            ok = false;
+            break;
           }
-          if constexpr (EPI == EPI_RELU_BITS) {
-            // mask of the activation as stored in dtype d0; no tile store
-            uint32_t bits = 0;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              float h = v[i];
-              if (p.d0 == DT_BF16) h = __bfloat162float(__float2bfloat16_rn(h));
-              bits |= (h > 0.f ? 1u : 0u) << i;
-            }
-            if (row < p.M)
-              static_cast<uint16_t*>(p.out0)[row * p.ld0 + (n0 + c) / 16] =
-                  static_cast<uint16_t>(bits);
-            continue;
+          uint8_t* st = St + static_cast<size_t>(stage) * stage_bytes;
+          mbar_expect_tx(full + stage, tx);
+          tma_load_2d(st, &tmA, full + stage, kb * kBK3, static_cast<int>(mt * kBM));
+          tma_load_2d(st + 3 * kAStage3, &tmBh, full + stage, kb * kBK3, n0);
+          tma_load_2d(st + 3 * kAStage3 + b_bytes, &tmBm, full + stage, kb * kBK3, n0);
+          tma_load_2d(st + 3 * kAStage3 + 2 * b_bytes, &tmBl, full + stage, kb * kBK3, n0);
+          armed |= 1u << stage;
+          last_par = (last_par & ~(1u << stage)) | (phase << stage);
+          if (++stage == p.stages) {
+            stage = 0;
+            phase ^= 1u;
           }
-          uint8_t* buf = stg + sb * kStgBytes;
-          // the tensor store that last read this buffer must be done with it
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          __syncwarp();
-          if ((which ? p.d1 : p.d0) == DT_BF16) stage_row_bf16(buf, lane, v);
-          else stage_row_f32(buf, lane, v);
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {  // rows past M are clipped by the tensor map
-            tma_store_2d(which ? &tmO1 : &tmO0, buf, col, static_cast<int>(row0));
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          }
-          sb ^= 1;
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty + acc);
+      if (!ok) {
+        // let our own copies land before the CTA's shared memory goes away
+        for (int s = 0; s < p.stages; ++s)
+          if (armed & (1u << s)) {
+            const uint32_t a = smem_u32(full + s);
+            for (uint32_t it = 0; it < kSpinLimit && !mbar_try(a, (last_par >> s) & 1u); ++it) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t blk = 0;  // k blocks issued so far (all tiles)
+      bool ok = true;
+      for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups) {
+        for (int kb = 0; kb < p.n_kb; ++kb, ++blk) {
+          const int b = static_cast<int>(blk & 1u);
+          if (!mbar_wait(tempty + b, ((blk >> 1) & 1u) ^ 1u, abort_flag) ||
+              !mbar_wait(conv + stage, phase, abort_flag)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_main = tmem_base + static_cast<uint32_t>(2 * b * p.acc_stride);
+          const uint32_t d_corr = d_main + static_cast<uint32_t>(p.acc_stride);
+          const uint32_t ah = smem_u32(St + static_cast<size_t>(stage) * stage_bytes);
+          const uint32_t am = ah + kAStage3;
+          const uint32_t al = ah + 2 * kAStage3;
+          const uint32_t bh = ah + 3 * kAStage3;
+          const uint32_t bm = bh + b_bytes;
+          const uint32_t bl = bh + 2 * b_bytes;
+#pragma unroll
+          for (int k = 0; k < kBK3 / 8; ++k) {  // 8 TF32 elements = 32 bytes per MMA
+            const uint32_t o = 32 * k;
+            // fresh sums per k block: the small products, then hi.hi alone
+            const uint32_t acc = k != 0 ? 1u : 0u;
+            umma_tf32(d_corr, desc_kmajor_sw128(am + o), desc_kmajor_sw128(bm + o), p.idesc, acc);
+            umma_tf32(d_corr, desc_kmajor_sw128(al + o), desc_kmajor_sw128(bh + o), p.idesc, 1u);
+            umma_tf32(d_corr, desc_kmajor_sw128(ah + o), desc_kmajor_sw128(bl + o), p.idesc, 1u);
+            umma_tf32(d_corr, desc_kmajor_sw128(am + o), desc_kmajor_sw128(bh + o), p.idesc, 1u);
+            umma_tf32(d_corr, desc_kmajor_sw128(ah + o), desc_kmajor_sw128(bm + o), p.idesc, 1u);
+            umma_tf32(d_main, desc_kmajor_sw128(ah + o), desc_kmajor_sw128(bh + o), p.idesc, acc);
+          }
+          umma_commit(empty + stage);
+          umma_commit(tfull + b);
+          if (++stage == p.stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp < 2 + kConvWarps) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 64;  // 0 .. 32 * kConvWarps - 1
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups) {
+      for (int kb = 0; kb < p.n_kb; ++kb) {
+        if (!mbar_wait(full + stage, phase, abort_flag)) {
+          if (lane == 0) give_up();
+          ok = false;
+          break;
+        }
+        float4* a = reinterpret_cast<float4*>(St + static_cast<size_t>(stage) * stage_bytes);
+        float4* amid = a + kAStage3 / 16;
+        float4* alo = a + 2 * (kAStage3 / 16);
+#pragma unroll 4
+        for (int i = ct; i < static_cast<int>(kAStage3 / 16); i += 32 * kConvWarps) {
+          const float4 v = a[i];
+          float4 h, m, l;
+          split3(v.x, h.x, m.x, l.x);
+          split3(v.y, h.y, m.y, l.y);
+          split3(v.z, h.z, m.z, l.z);
+          split3(v.w, h.w, m.w, l.w);
+          a[i] = h;
+          amid[i] = m;
+          alo[i] = l;
+        }
+        // the MMAs read this stage through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv + stage);
+        if (++stage == p.stages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+  } else {
+    // ---------------- accumulation and epilogue ----------------
+    const int ew = warp - 2 - kConvWarps;
+    const int quarter = warp & 3;                 // TMEM lanes this warp may read
+    constexpr int parts = kEpiWarps3 / 4;         // column parts per lane quarter
+    const int nch = p.BN / 16;
+    const int ch0 = nch * (ew >> 2) / parts;      // this warp's 16-column chunks
+    const int nmine = nch * ((ew >> 2) + 1) / parts - ch0;  // at most 4 (BN <= 128)
+    uint8_t* stg = Stg + static_cast<size_t>(ew) * 2 * kStgBytes;
+    int sb = 0;
+    uint32_t blk = 0;
+    bool ok = true;
+    for (int64_t mt = group; ok && mt < p.m_tiles; mt += groups) {
+      float acc[4][16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[q][i] = 0.f;
+      for (int kb = 0; kb < p.n_kb; ++kb, ++blk) {
+        const int b = static_cast<int>(blk & 1u);
+        if (!mbar_wait(tfull + b, (blk >> 1) & 1u, abort_flag)) {
+          if (lane == 0) give_up();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                               static_cast<uint32_t>(2 * b * p.acc_stride + 16 * ch0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // main and correction sums of one chunk per wait
+          if (q >= nmine) break;
+          uint32_t rm[16], rc[16];
+          tmem_ld16_issue(taddr + static_cast<uint32_t>(16 * q), rm);
+          tmem_ld16_issue(taddr + static_cast<uint32_t>(p.acc_stride + 16 * q), rc);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            acc[q][i] += __uint_as_float(rm[i]) + __uint_as_float(rc[i]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty + b);
+      }
+      if (!ok) break;
+      const int64_t row0 = mt * kBM + quarter * 32;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 16 * (ch0 + q);
+        if (q < nmine && n0 + c < p.Nc)  // ragged last n tile: nothing stored past Nc
+          epilogue_chunk<EPI>(p, &tmO0, &tmO1, stg, sb, lane, row0, n0, c, acc[q]);
+      }
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     __syncwarp();
@@ -732,6 +1063,7 @@ tc_wgrad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
 bool g_ok = false;
+bool g_tf32_ok = false;
 int g_max_smem = 0;
 
 void init_driver() {
@@ -765,6 +1097,20 @@ void init_driver() {
     cudaGetLastError();
     return;
   }
+  // the split-TF32 kernels of the FP32 form (optional: without them that
+  // form stays on CUDA cores)
+  g_tf32_ok =
+      cudaFuncSetAttribute(tc3_gemm_nt_kernel<EPI_BIAS_RELU>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) == cudaSuccess &&
+      cudaFuncSetAttribute(tc3_gemm_nt_kernel<EPI_BIAS_SIGMOID>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) == cudaSuccess &&
+      cudaFuncSetAttribute(tc3_gemm_nt_kernel<EPI_SPLIT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) == cudaSuccess &&
+      cudaFuncSetAttribute(tc3_gemm_nt_kernel<EPI_RELU_BITS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) == cudaSuccess &&
+      cudaFuncSetAttribute(tc3_gemm_nt_kernel<EPI_BIAS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem) == cudaSuccess;
+  if (!g_tf32_ok) cudaGetLastError();
   g_ok = true;
 }
 
@@ -777,6 +1123,22 @@ bool make_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int6
   cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 2-D FP32 tensor map over a row-major matrix: inner extent `cols`
+// elements, `rows` rows, row pitch `ld` elements; box kBK3 x box_rows
+// (128 bytes of K per row, 128-byte swizzle).
+bool make_map_f32(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                  int box_rows) {
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK3), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -960,6 +1322,115 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
       break;
     default:
       tc_gemm_nt_kernel<EPI_SPLIT><<<grid, kThreads, smem, st>>>(ta, tb, to0, to1, p);
+      break;
+  }
+  return 1;
+}
+
+bool tc3_gemm_supported(const GemmArgs& g) {
+  if (!g_ok || !g_tf32_ok) return false;
+  if (g.da != DT_F32 || g.db != DT_F32 || !g.a_kmajor || !g.b_kmajor || !g.B_mid || !g.B_lo)
+    return false;
+  if (g.epi != EPI_BIAS_RELU && g.epi != EPI_BIAS_SIGMOID && g.epi != EPI_SPLIT &&
+      g.epi != EPI_RELU_BITS && g.epi != EPI_BIAS)
+    return false;
+  if (g.K < kBK3 || g.K % 4 || g.lda % 4 || g.ldb % 4 || g.Nc % 16) return false;
+  if (g.epi == EPI_SPLIT && g.split % 16) return false;
+  if ((g.epi != EPI_RELU_BITS && g.ld0 % 4) || (g.epi == EPI_SPLIT && g.ld1 % 4)) return false;
+  // tensor maps need 16-byte aligned bases
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+  if (!al16(g.A) || !al16(g.B) || !al16(g.B_mid) || !al16(g.B_lo) ||
+      (g.epi != EPI_RELU_BITS && !al16(g.out0)) ||
+      (g.epi == EPI_SPLIT && !al16(g.out1)))
+    return false;
+  // at least two pipeline stages
+  const int bn = g.Nc < kBN3 ? g.Nc : kBN3;
+  const size_t stage_bytes = 3 * static_cast<size_t>(kAStage3) + 3 * static_cast<size_t>(bn) * kBK3 * 4;
+  return static_cast<size_t>(g_max_smem) >= 1024 + kStgTotal3 + 256 + 2 * stage_bytes;
+}
+
+int tc3_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
+  TcParams p;
+  p.M = g.M;
+  p.Nc = g.Nc;
+  p.K = static_cast<int>(g.K);
+  p.BN = g.Nc < kBN3 ? g.Nc : kBN3;
+  p.stream_b = 1;
+  p.n_tiles_n = (g.Nc + p.BN - 1) / p.BN;
+  p.n_kb = (p.K + kBK3 - 1) / kBK3;
+  p.m_tiles = (g.M + kBM - 1) / kBM;
+  const size_t stage_bytes = 3 * static_cast<size_t>(kAStage3) + 3 * static_cast<size_t>(p.BN) * kBK3 * 4;
+  const size_t fixed = 1024 + kStgTotal3 + 256;
+  int stages = static_cast<int>((static_cast<size_t>(g_max_smem) - fixed) / stage_bytes);
+  stages = stages > 4 ? 4 : stages;
+  if (stages < 2) {  // excluded by tc3_gemm_supported
+    flag_error_launch(g.err_flag, 4, st);
+    return 1;
+  }
+  p.stages = stages;
+  size_t smem = fixed + static_cast<size_t>(stages) * stage_bytes;
+  if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA (one TMEM allocation) per SM
+  p.acc_stride = (p.BN + 31) / 32 * 32;
+  int cols = 32;
+  while (cols < 4 * p.acc_stride) cols <<= 1;  // two (main, correction) pairs
+  p.tmem_cols = cols;
+  // D FP32, A and B TF32, both K-major, N = BN, M = 128
+  p.idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(p.BN >> 3) << 17) |
+            (static_cast<uint32_t>(kBM >> 4) << 24);
+  p.epi = g.epi;
+  p.bias = g.bias;
+  p.out0 = g.out0;
+  p.ld0 = g.ld0;
+  p.d0 = g.d0;
+  p.out1 = g.out1;
+  p.ld1 = g.ld1;
+  p.d1 = g.d1;
+  p.split = g.split;
+  p.row_scale = g.row_scale;
+  p.addend = g.addend;
+  p.ld_add = g.ld_add;
+  p.d_add = g.d_add;
+  p.n_valid = g.n_valid > 0 ? g.n_valid : g.Nc;
+  p.err_flag = g.err_flag;
+  CUtensorMap ta, tbh, tbm, tbl, to0, to1;
+  const int64_t cols0 = g.epi == EPI_SPLIT ? g.split : g.Nc;
+  bool ok = make_map_f32(&ta, g.A, g.K, g.M, g.lda, kBM) &&
+            make_map_f32(&tbh, g.B, g.K, g.Nc, g.ldb, p.BN) &&
+            make_map_f32(&tbm, g.B_mid, g.K, g.Nc, g.ldb, p.BN) &&
+            make_map_f32(&tbl, g.B_lo, g.K, g.Nc, g.ldb, p.BN);
+  if (ok) {
+    if (g.epi == EPI_RELU_BITS) to0 = tbh;  // bits are stored directly; map unused
+    else ok = make_out_map(&to0, g.out0, g.d0, cols0, g.M, g.ld0);
+  }
+  if (ok) {
+    if (g.epi == EPI_SPLIT) ok = make_out_map(&to1, g.out1, g.d1, g.Nc - g.split, g.M, g.ld1);
+    else to1 = to0;
+  }
+  if (!ok) {
+    // a rejected descriptor: B holds only the hi part here, so no CUDA-core
+    // product could stand in; the step reports the failure
+    flag_error_launch(g.err_flag, 4, st);
+    return 1;
+  }
+  int groups = num_sms / p.n_tiles_n;
+  if (groups < 1) groups = 1;
+  if (groups > p.m_tiles) groups = static_cast<int>(p.m_tiles);
+  const int grid = groups * p.n_tiles_n;
+  switch (g.epi) {
+    case EPI_BIAS_RELU:
+      tc3_gemm_nt_kernel<EPI_BIAS_RELU><<<grid, kThreads3, smem, st>>>(ta, tbh, tbm, tbl, to0, to1, p);
+      break;
+    case EPI_BIAS_SIGMOID:
+      tc3_gemm_nt_kernel<EPI_BIAS_SIGMOID><<<grid, kThreads3, smem, st>>>(ta, tbh, tbm, tbl, to0, to1, p);
+      break;
+    case EPI_RELU_BITS:
+      tc3_gemm_nt_kernel<EPI_RELU_BITS><<<grid, kThreads3, smem, st>>>(ta, tbh, tbm, tbl, to0, to1, p);
+      break;
+    case EPI_BIAS:
+      tc3_gemm_nt_kernel<EPI_BIAS><<<grid, kThreads3, smem, st>>>(ta, tbh, tbm, tbl, to0, to1, p);
+      break;
+    default:
+      tc3_gemm_nt_kernel<EPI_SPLIT><<<grid, kThreads3, smem, st>>>(ta, tbh, tbm, tbl, to0, to1, p);
       break;
   }
   return 1;

@@ -97,6 +97,63 @@ __global__ void weight_shadows_kernel(const float* __restrict__ th, int H0, int 
   }
 }
 
+// The dense weights split exactly into three TF32 parts (split3) for the FP32
+// form's tensor-core GEMMs, written like the BF16 shadows (32 x 32 tiles
+// through shared memory, both orientations).
+struct SplitOut {
+  float* W1[3];
+  float* W1t[3];
+  float* W2[3];
+  float* W2t[3];
+};
+
+__global__ void weight_split_kernel(const float* __restrict__ th, int H0, int H1, int S,
+                                    int S_pad, SplitOut o) {
+  __shared__ float tile[3][32][33];
+  const int K1 = 2 * H0, K2 = 2 * H1;
+  const int tc1 = (K1 + 31) / 32, tr1 = (H1 + 31) / 32;
+  const int tc2 = (K2 + 31) / 32;
+  const int64_t t1 = (int64_t)tr1 * tc1;
+  const int64_t t = blockIdx.x;
+  const float* src;
+  float* const* ds;
+  float* const* dt;
+  int rows, cols, valid_rows, tcn;
+  int64_t tt;
+  if (t < t1) {
+    src = th; ds = o.W1; dt = o.W1t; rows = H1; valid_rows = H1; cols = K1; tt = t; tcn = tc1;
+  } else {
+    src = th + (int64_t)H1 * K1 + H1; ds = o.W2; dt = o.W2t; rows = S_pad; valid_rows = S;
+    cols = K2; tt = t - t1; tcn = tc2;
+  }
+  const int r0 = (int)(tt / tcn) * 32, c0 = (int)(tt % tcn) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int y = ty; y < 32; y += 8) {
+    const int r = r0 + y, c = c0 + tx;
+    if (r < rows && c < cols) {
+      float part[3];
+      split3(r < valid_rows ? src[(int64_t)r * cols + c] : 0.f, part[0], part[1], part[2]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ds[k][(int64_t)r * cols + c] = part[k];
+        tile[k][y][tx] = part[k];
+      }
+    }
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {  // transposed: row c, columns r
+    const int c = c0 + y, r = r0 + tx;
+    if (r < rows && c < cols) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dt[k][(int64_t)c * rows + r] = tile[k][tx][y];
+    }
+  }
+}
+
+__global__ void flag_error_kernel(int* flag, int bits) {
+  if (flag) atomicOr(flag, bits);
+}
+
 __global__ void init_uniform_kernel(float* p, int64_t n, float bound, uint64_t seed,
                                     uint64_t tag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -288,6 +345,24 @@ void weight_shadows_launch(const float* theta, int H0, int H1, int S, int S_pad,
   weight_shadows_kernel<<<(unsigned)tiles, 256, 0, st>>>(
       theta, H0, H1, S, S_pad, static_cast<bf16*>(W1s), static_cast<bf16*>(W1t),
       static_cast<bf16*>(W2s), static_cast<bf16*>(W2t));
+}
+
+void weight_split_launch(const float* theta, int H0, int H1, int S, int S_pad, float* const* W1,
+                         float* const* W1t, float* const* W2, float* const* W2t, cudaStream_t st) {
+  const int64_t tiles = (int64_t)((H1 + 31) / 32) * ((2 * H0 + 31) / 32) +
+                        (int64_t)((S_pad + 31) / 32) * ((2 * H1 + 31) / 32);
+  SplitOut o;
+  for (int k = 0; k < 3; ++k) {
+    o.W1[k] = W1[k];
+    o.W1t[k] = W1t[k];
+    o.W2[k] = W2[k];
+    o.W2t[k] = W2t[k];
+  }
+  weight_split_kernel<<<(unsigned)tiles, 256, 0, st>>>(theta, H0, H1, S, S_pad, o);
+}
+
+void flag_error_launch(int* flag, int bits, cudaStream_t st) {
+  flag_error_kernel<<<1, 1, 0, st>>>(flag, bits);
 }
 
 void init_uniform_launch(float* p, int64_t n, float bound, uint64_t seed, uint64_t tag,

@@ -230,6 +230,9 @@ struct GemmArgs {
   int64_t ldb = 0;
   int db = DT_F32;
   int b_kmajor = 1;
+  // split-TF32 tensor-core path: mid and lo parts of B (B holds the hi part)
+  const void* B_mid = nullptr;
+  const void* B_lo = nullptr;
   int epi = EPI_PARTIAL;
   const float* bias = nullptr;
   void* out0 = nullptr;
@@ -311,6 +314,15 @@ void copy_rows_launch(int64_t N, int H, const float* src, void* dst, int64_t ldd
 //   W2s [S_pad x 2H1] = Wcat2 (pad rows 0), W2t [2H1 x S_pad] = Wcat2^T (pad cols 0).
 void weight_shadows_launch(const float* theta, int H0, int H1, int S, int S_pad,
                            void* W1s, void* W1t, void* W2s, void* W2t, cudaStream_t st);
+// FP32 form on the tensor cores: the dense weights split exactly into three
+// TF32 parts (split3: hi, mid, lo), in the layouts of the BF16 shadows (W1:
+// H1 x 2H0 and its transpose; W2: S_pad x 2H1, rows past S zero, and its
+// transpose).  W[k] is part k (0 hi, 1 mid, 2 lo); Wt[k] its transpose.
+void weight_split_launch(const float* theta, int H0, int H1, int S, int S_pad, float* const* W1,
+                         float* const* W1t, float* const* W2, float* const* W2t, cudaStream_t st);
+// ORs bits into the device error word (bit 2, value 4: a kernel could not be
+// set up and its product was not computed).
+void flag_error_launch(int* flag, int bits, cudaStream_t st);
 void init_uniform_launch(float* p, int64_t n, float bound, uint64_t seed,
                          uint64_t tag, cudaStream_t st);
 void init_normal_launch(float* p, int64_t n, uint64_t seed, uint64_t tag,

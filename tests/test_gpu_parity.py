@@ -230,7 +230,8 @@ STEP_CASES = [
 ]
 
 
-def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None, plain=False):
+def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None, plain=False,
+                   fp32_engine=0):
     """One GPU step from seeded state and the oracle's step from the same
     state.  With plain=True the BF16 form is also compared with the oracle
     that decides the ReLU signs on FP64 Z1 (out["ref_plain"])."""
@@ -246,7 +247,7 @@ def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=No
     solver = cpra.Solver(rp, col, lam=lam if problem == O.MIS else None, problem=problem, S=S,
                          H0=H, H1=H, alpha=alpha, precision=precision, nu=nu,
                          diversity_kind=div, gamma0=-1.0, gamma1=1.0, schedule_steps=T,
-                         keep_emb_grad=keep_emb_grad, recompute=recompute)
+                         keep_emb_grad=keep_emb_grad, recompute=recompute, fp32_engine=fp32_engine)
     for which, arr in ((cpra.T_THETA, theta), (cpra.T_EMB, X0), (cpra.T_THETA_M, mt),
                        (cpra.T_THETA_V, vt), (cpra.T_EMB_M, mx), (cpra.T_EMB_V, vx),
                        (cpra.T_STEP, np.array([t_prev]))):
@@ -324,9 +325,12 @@ def _check_step(out, ref, g, lam, gamma, theta, X0, S, H, tol, problem):
         assert np.linalg.norm(out["X0"].reshape(X0.shape) - ref["X0_next"]) <= 10 * tol * np.linalg.norm(dref)
 
 
+@pytest.mark.parametrize("engine", [cpra.FP32_TENSOR, cpra.FP32_CUDA_CORES])
 @pytest.mark.parametrize("case", STEP_CASES)
-def test_full_step_fp32_matches_oracle(case):
-    out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, cpra.FP32)
+def test_full_step_fp32_matches_oracle(case, engine):
+    """Both engines of the FP32 form: split-TF32 tensor-core GEMMs (the
+    default) and CUDA-core GEMMs, each within 1e-5 of the FP64 oracle."""
+    out, ref, g, lam, gamma, theta, X0 = _run_step_case(case, cpra.FP32, fp32_engine=engine)
     problem, S, H = case[0], case[4], case[5]
     _check_step(out, ref, g, lam, gamma, theta, X0, S, H, 1e-5, problem)
     # rounding: bit-exact wherever the FP64 P is not within tolerance of 0.5
