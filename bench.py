@@ -54,6 +54,9 @@ WORKLOADS = {
     "mis_rrg5_n2e5_s256_h128_bf16": dict(graph="rrg", N=2 * 10**5, d=5, seed=5, problem=0, S=256,
                                          H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
                                          div=0, recompute=1),
+    "mis_rrg5_n2e5_s256_h128_fp32": dict(graph="rrg", N=2 * 10**5, d=5, seed=5, problem=0, S=256,
+                                         H=128, lam=("geom", 0.5, 10.0), nu=0.0, precision=0,
+                                         div=0, recompute=1),
     "mis_rrg20_n1e4_s100_h256_bf16": dict(graph="rrg", N=10**4, d=20, seed=2, problem=0, S=100,
                                           H=256, lam=("geom", 0.5, 10.0), nu=0.0, precision=1,
                                           div=0, recompute=0),
@@ -345,10 +348,10 @@ def run_gpu(args):
     d2h = (3 * S + 1) * 4 + (S * 24 + 8) / args.steps
 
     # the plain FP32 form (every dense layer in FP32) on the same graph and
-    # shots, timed the same way: the comparator of the BF16 form
-    fp32_form = None
-    if w["precision"] == 1 and not args.no_fp32_form:
-        s3 = cpra.Solver(rp, col, lam=lam, **dict(kw, precision=0))
+    # shots, timed the same way: the comparator of the BF16 form, with each
+    # of its two engines
+    def time_fp32(engine):
+        s3 = cpra.Solver(rp, col, lam=lam, **dict(kw, precision=0, fp32_engine=engine))
         for t in range(args.warmup):
             s3.step(t)
         torch.cuda.synchronize()
@@ -361,11 +364,19 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ms32 = max_over_ranks(e0.elapsed_time(e1), dist)
         s3.close()
-        fp32_form = {"ms_per_step": ms32 / args.steps,
-                     "value": replica_throughput(world, nnz * S * args.steps, ms32 / 1e3),
-                     "unit": METRIC, "steps": args.steps, "warmup": args.warmup,
-                     "how": "the same workload with precision fp32 (all dense layers fp32), "
-                            "per-step launches, CUDA events on the library stream"}
+        return {"ms_per_step": ms32 / args.steps,
+                "value": replica_throughput(world, nnz * S * args.steps, ms32 / 1e3),
+                "unit": METRIC, "steps": args.steps, "warmup": args.warmup}
+
+    fp32_form = None
+    if w["precision"] == 1 and not args.no_fp32_form:
+        fp32_form = time_fp32(cpra.FP32_TENSOR)
+        fp32_form["how"] = ("the same workload with precision fp32: dense layers and input "
+                            "gradients as split-TF32 tensor-core GEMMs (FP32-accurate), weight "
+                            "gradients on CUDA cores; per-step launches, CUDA events on the "
+                            "library stream")
+        fp32_form["cuda_cores"] = time_fp32(cpra.FP32_CUDA_CORES)
+        fp32_form["cuda_cores"]["how"] = "the same with every dense product on CUDA cores"
 
     value = replica_throughput(world, nnz * S * args.steps, ms / 1e3)
     peak, peak_src = read_peaks()
