@@ -428,6 +428,9 @@ def run_gpu(args):
         "best_eval": {"max_objective_feasible": int(max(
             [r["objective"] for r in rec if r["violations"] == 0] or [-1]))},
     }
+    if world == 1 and w["precision"] == 1 and not args.no_quality:
+        # the time-to-quality half of the metric, in compact form
+        line["quality_compact"] = run_quality_compact(args)
     if rank == 0:
         line["cpu_baseline"] = run_cpu_baseline(args.workload) if not args.no_cpu else None
         if not args.no_cpu and world == 1:
@@ -641,6 +644,63 @@ def run_quality(args):
     print(json.dumps(out))
 
 
+def run_quality_compact(args):
+    """A compact form of the time-to-quality race for the default line: MIS on
+    a seeded 5-regular graph of 2*10^5 nodes (S = 256, H = 128, the default
+    workload's shots and widths), 2000-step schedules, evaluation every 50
+    steps; the warm-start network trained on 96 small graphs (N 1,000-5,000,
+    1000-step targets).  Arms as in --quality: FP32 (split-TF32 engine), BF16
+    plain, BF16 plain with the warm arm's schedule, BF16 + warm start."""
+    import torch
+    from paper_2402_02190_gb300 import cpra
+    from paper_2402_02190_gb300 import warm as WM
+    S, H, steps, ev = 256, 128, 2000, 50
+    n_train, target_steps = 96, 1000
+    lam = I.lambda_geomspace(0.5, 10.0, S)
+    g0 = args.q_warm_gamma0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    graphs = WM.training_graphs(n_train, seed=78, n_min=1000, n_max=5000)
+    dataset = []
+    for k, (rp, col, d) in enumerate(graphs):
+        bits, _ = WM.cpra_targets(rp, col, S, lam, target_steps, cpra.BF16, H=64, seed=k + 1)
+        dataset.append((rp, col, bits, 2000 + k))
+    net = cpra.WarmStartNet(max(len(g[0]) - 1 for g in graphs) * 8,
+                            max(int(g[0][-1]) for g in graphs) * 8, F=16, H=64, S=S,
+                            precision=cpra.BF16, lr=3e-3)
+    WM.train_network(net, dataset, 40, 8)
+    theta = net.params(0)
+    net.close()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rp, col = I.random_regular_graph(2 * 10**5, 5, seed=55)
+    fp32 = WM.run_trace(rp, col, S, lam, steps, ev, cpra.FP32, H=H, seed=1)
+    target = 0.99 * fp32[-1][2]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    big = cpra.WarmStartNet(len(rp) - 1, int(rp[-1]), F=16, H=64, S=S, precision=cpra.BF16)
+    big.set_params(theta)
+    L0 = WM.predict_logits(big, rp, col, 99)
+    warm = WM.run_trace(rp, col, S, lam, steps, ev, cpra.BF16, H=H, seed=1, init_logits=L0,
+                        gamma0=g0, t0=t0)
+    big.close()
+    plain = WM.run_trace(rp, col, S, lam, steps, ev, cpra.BF16, H=H, seed=1)
+    matched = WM.run_trace(rp, col, S, lam, steps, ev, cpra.BF16, H=H, seed=1, gamma0=g0)
+
+    def arm(tr):
+        r = WM.time_to_reach(tr, target)
+        return {"seconds_to_99pct": r[0] if r else None, "steps_to_99pct": r[1] if r else None,
+                "best": tr[-1][2]}
+    return {"metric": "wall seconds to within 1% of the FP32 form's best MIS", "unit": "s",
+            "graph": "rrg degree 5, N=200000, seed 55", "S": S, "H": H, "steps": steps,
+            "eval_every": ev, "warm_gamma0": g0,
+            "warm_training": {"graphs": n_train, "target_steps": target_steps, "seconds": t_train},
+            "fp32": arm(fp32), "bf16_plain": arm(plain), "bf16_plain_matched_schedule": arm(matched),
+            "bf16_warm": arm(warm),
+            "how": "compact form of bench.py --quality; wall clock from context creation "
+                   "(the warm arm includes its network inference)"}
+
+
 # ------------------------------------------------------------ two-stage mode
 def run_two_stage_bench(args):
     """The two-stage experiment's shape (App. two-stage): weighted-MIS tasks on
@@ -744,6 +804,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32-form", action="store_true",
                     help="skip timing the FP32 form of a BF16 workload")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the compact time-to-quality race of the default line")
     ap.add_argument("--recompute", type=int, choices=[0, 1], default=None,
                     help="override the workload's activation-recompute setting")
     ap.add_argument("--graph", action="store_true",
