@@ -1163,10 +1163,11 @@ bool make_out_map(CUtensorMap* m, const void* base, int dt, int64_t cols, int64_
 }
 
 // Shared memory a CTA needs with BN output columns (weights resident) and
-// the minimum of two A stages.
-size_t tc_smem_need(int bn, int64_t K) {
+// `stages` A stages (two at least).
+size_t tc_smem_need(int bn, int64_t K, int stages = 2) {
   const int n_kb = static_cast<int>((K + kBK - 1) / kBK);
-  return 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal + 2 * kStageBytes + 256;
+  return 1024 + static_cast<size_t>(n_kb) * bn * kBK * 2 + kStgTotal +
+         static_cast<size_t>(stages) * kStageBytes + 256;
 }
 
 // Shared memory with BN columns when the weights stream with the A stages
@@ -1191,10 +1192,21 @@ struct NPlan {
 // slowest CTA runs ceil(m_tiles / groups) tiles of cost ~ bn (a product with
 // few m tiles, like the 2500-row DBM layers, otherwise leaves SMs idle for a
 // whole tile).  bn = 0: no plan fits.
-NPlan plan_n(int Nc, int64_t K, int64_t M = 0, int num_sms = 0) {
+NPlan plan_n(int Nc, int64_t K, int64_t M = 0, int num_sms = 0, bool deep = false) {
   NPlan pl;
   const int cap = Nc < 256 ? Nc : 256;
   const int want = cap < 128 ? cap : 128;
+  // deep: resident weights with a pipeline at least four A stages deep, on
+  // equal n tiles.  A 256-wide tile of a K = 256 product keeps only two
+  // stages; for the sigmoid head (FP32 output) two 128-wide tiles that share
+  // each A tile through L2 measured faster (0.283 -> 0.258 ms at N = 10^6),
+  // for the split input gradient (BF16 outputs) slower (0.204 -> 0.215 ms).
+  if (deep)
+    for (int bn = cap; bn >= want; bn -= 16)
+      if (Nc % bn == 0 && tc_smem_need(bn, K, 4) <= static_cast<size_t>(g_max_smem)) {
+        pl.bn = bn;
+        return pl;
+      }
   for (int bn = cap; bn >= want; bn -= 16)
     if (tc_smem_need(bn, K) <= static_cast<size_t>(g_max_smem)) {
       pl.bn = bn;
@@ -1250,7 +1262,7 @@ int tc_gemm_launch(const GemmArgs& g, int num_sms, cudaStream_t st) {
   p.M = g.M;
   p.Nc = g.Nc;
   p.K = static_cast<int>(g.K);
-  const NPlan pl = plan_n(g.Nc, g.K, g.M, num_sms);
+  const NPlan pl = plan_n(g.Nc, g.K, g.M, num_sms, g.epi == EPI_BIAS_SIGMOID);
   p.BN = pl.bn;
   p.stream_b = pl.stream ? 1 : 0;
   p.n_tiles_n = (g.Nc + p.BN - 1) / p.BN;
