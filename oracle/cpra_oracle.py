@@ -418,7 +418,8 @@ def integer_eval(g: Graph, X, lam, problem, weights=None, inst=None):
     """Per shot: objective (MIS set size / MaxCut cut size), violations
     (MIS: edges with both ends selected; MaxCut: 0), qubo value l(x), the
     objective in the problem's own units `value` (set size, total weight of
-    the set for weighted MIS, cut size), and the pairwise Hamming sum
+    the set for weighted MIS, cut weight sum_{cut edges} A_ij for MaxCut --
+    the cut size with unit weights), and the pairwise Hamming sum
     sum_{s<l} d_H(x_s, x_l).  DBM: objective = matched pairs sum x, violations =
     rows and columns with more than one pair plus the two diversity
     constraints that fail, value = sum C x, qubo = l(x)."""
@@ -444,8 +445,8 @@ def integer_eval(g: Graph, X, lam, problem, weights=None, inst=None):
     else:
         obj = (Xi != Xj).sum(axis=0)
         viol = np.zeros(S, dtype=np.int64)
-        qubo = -(g.ew[:, None] * (Xi != Xj)).sum(axis=0)
-        value = obj.astype(np.float64)
+        value = (g.ew[:, None] * (Xi != Xj)).sum(axis=0)   # the (weighted) cut
+        qubo = -value
     k = X.sum(axis=1)
     pair_hamming = int((k * (S - k)).sum())
     return dict(objective=obj.astype(np.int64), violations=viol.astype(np.int64),

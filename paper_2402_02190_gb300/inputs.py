@@ -149,6 +149,27 @@ def bfs_induced_subgraph(rowptr, col, n_keep: int, root: int = 0):
     return edges_to_csr(len(order), seen[ei[keep]], seen[ej[keep]])
 
 
+def seeded_edge_weights(rowptr, col, seed: int, kind: str = "uniform") -> np.ndarray:
+    """Symmetric edge weights per CSR entry (w_ij = w_ji), float32: "uniform"
+    draws U(0.5, 2) per undirected edge, "pm1" draws +1 or -1 (the signed
+    unit weights of some Gset max-cut instances)."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    N = len(rowptr) - 1
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(rowptr))
+    lo, hi = np.minimum(rows, col), np.maximum(rows, col)
+    keys = lo * N + hi
+    uniq, inv = np.unique(keys, return_inverse=True)
+    rng = np.random.default_rng(seed)
+    if kind == "uniform":
+        per_edge = rng.uniform(0.5, 2.0, size=len(uniq))
+    elif kind == "pm1":
+        per_edge = rng.choice(np.array([-1.0, 1.0]), size=len(uniq))
+    else:
+        raise ValueError("kind")
+    return per_edge[inv].astype(np.float32)
+
+
 def lambda_linspace(lo: float, hi: float, S: int) -> np.ndarray:
     return np.linspace(lo, hi, S).astype(np.float32)
 
