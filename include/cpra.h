@@ -159,8 +159,17 @@ CPRA_API int64_t cpra_param_count_for(int32_t H0, int32_t H1, int32_t S);
 CPRA_API size_t cpra_workspace_bytes(int64_t N, int64_t nnz, const cpra_config* cfg);
 
 /* Creates a context: validates and uploads the graph (host CSR, see
-   conventions; w must be NULL -- unit weights), copies cfg and lambda, and
-   initialises theta ~ U(+-1/sqrt(fan_in)) and h^0 ~ N(0,1) from cfg->seed.
+   conventions), copies cfg and lambda, and initialises theta ~
+   U(+-1/sqrt(fan_in)) and h^0 ~ N(0,1) from cfg->seed.
+   w: host float[nnz], the edge weight A_ij of each CSR entry, or NULL for
+   unit weights.  Weights enter the MaxCut QUBO of Table objective-functions,
+   sum_{i<j} A_ij (2 x_i x_j - x_i - x_j): the relaxed cost, its gradient
+   2 (A P)_i - sum_j A_ij, and the records (objective = number of cut edges,
+   value = cut weight sum of A_ij over cut edges in FP64, qubo = -value;
+   cpra_solve ranks shots by value).  The GNN's mean aggregation stays
+   unweighted.  They must be finite and symmetric (the two entries of an
+   edge equal); with another problem, or otherwise, CPRA_EINVAL.  The
+   context keeps a device copy (its own allocation, freed by cpra_destroy).
    dev_workspace: device buffer of >= cpra_workspace_bytes() bytes owned by
    the caller for the context's lifetime, or NULL to let the library
    allocate (and free in cpra_destroy).  cuda_stream: cudaStream_t to order

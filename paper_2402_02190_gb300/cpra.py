@@ -192,10 +192,12 @@ def cpra_workspace_bytes(N: int, nnz: int, cfg: Config) -> int:
     return int(lib().cpra_workspace_bytes(N, nnz, C.byref(cfg)))
 
 
-def cpra_init_graph(rowptr, col, cfg: Config, lam=None, workspace=None, stream=None):
+def cpra_init_graph(rowptr, col, cfg: Config, lam=None, workspace=None, stream=None,
+                    weights=None):
     """Returns (ctx handle, workspace tensor or None).  ``workspace`` may be a
     torch uint8 CUDA tensor; with ``workspace='torch'`` one of the right size
-    is allocated by PyTorch's caching allocator."""
+    is allocated by PyTorch's caching allocator.  ``weights``: per-CSR-entry
+    edge weights A_ij (MaxCut), or None for unit weights."""
     import torch
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -214,8 +216,14 @@ def cpra_init_graph(rowptr, col, cfg: Config, lam=None, workspace=None, stream=N
         workspace = torch.empty(nb, dtype=torch.uint8, device="cuda")
     if workspace is not None:
         ws_ptr, ws_bytes = C.c_void_p(workspace.data_ptr()), workspace.numel()
+    w_arr = None
+    if weights is not None:
+        w_arr = np.ascontiguousarray(weights, dtype=np.float32)
+        if w_arr.size != col.size:
+            raise ValueError("weights must have one entry per CSR entry")
     h = C.c_void_p()
-    st = lib().cpra_init_graph(C.byref(h), N, _ptr(rowptr), _ptr(col) if col.size else None, None,
+    st = lib().cpra_init_graph(C.byref(h), N, _ptr(rowptr), _ptr(col) if col.size else None,
+                               _ptr(w_arr) if w_arr is not None and w_arr.size else None,
                                C.byref(cfg), ws_ptr, ws_bytes, _stream_handle(stream))
     cfg.lambda_ = None
     _check(st)
@@ -452,7 +460,7 @@ def cpra_op_round_eval(rowptr32, col32, P, S, lam, problem, x_bits, out_records,
 class Solver:
     """One CPRA context on the current CUDA device."""
 
-    def __init__(self, rowptr, col, lam=None, stream=None, **cfg_kw):
+    def __init__(self, rowptr, col, lam=None, stream=None, weights=None, **cfg_kw):
         import torch
         self.cfg = make_config(**cfg_kw)
         self.N = len(rowptr) - 1
@@ -461,7 +469,7 @@ class Solver:
         # work on, so torch events recorded on it time the library's kernels.
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.ctx, self._ws = cpra_init_graph(rowptr, col, self.cfg, lam=lam, workspace="torch",
-                                             stream=self.stream)
+                                             stream=self.stream, weights=weights)
 
     def step(self, t: int, want_terms: bool = False):
         return cpra_step(self.ctx, t, want_terms)

@@ -125,6 +125,13 @@ struct cpra_ctx {
   double* wv_part = nullptr;      // weighted MIS: per-block value partials
   double* wvalue = nullptr;       // weighted MIS: per-shot value
   bool wmis = false;
+  // MaxCut with edge weights A_ij (own allocation): weight per CSR entry,
+  // weighted degree per node, per-block cut-weight partials, cut weight per shot
+  void* ew_mem = nullptr;
+  float* ew_d = nullptr;
+  float* wdeg_d = nullptr;
+  double* cut_part = nullptr;
+  double* cutw = nullptr;
   DbmDev dbm;                     // matching instances (problem DBM)
   void* dbm_mem = nullptr;        // own cudaMalloc behind dbm, null until cpra_set_dbm
   int64_t dbm_bytes = 0;
@@ -596,6 +603,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     a.problem = dbm ? 2 : c->cfg.problem == CPRA_MAXCUT ? 1 : 0;
     a.dbm = c->dbm;
     a.w = c->w_d; a.ldw = c->S_pad;
+    a.ew = c->ew_d; a.wdeg = c->wdeg_d;
     a.alpha = c->cfg.alpha; a.div_kind = c->cfg.diversity_kind;
     a.grad_kind = 0; a.gamma = gamma; a.sc = do_loss ? sc : nullptr; a.nu = c->cfg.nu;
     a.G = c->GZ2; a.dg = c->act_dt; a.xbits = c->xbits;
@@ -623,13 +631,19 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
                             c->wvalue, c->stream);
       c->launches += 2;
     }
+    if (c->ew_d) {  // weighted MaxCut: the cut weight of each shot
+      weighted_cut_launch(N, c->S, c->rowptr, c->col, c->ew_d, c->xbits, c->cut_part, kWvBlocks,
+                          c->cutw, c->stream);
+      c->launches += 2;
+    }
     if (dbm) {  // matchings: line counts, constraints and rewards (the set size and
                 // pair-Hamming counters above are problem-independent)
       dbm_eval_launch(c->dbm, c->S, c->xbits, c->counters, c->eval_rec, c->ham_d, c->stream);
       c->launches += 3;
     } else {
       eval_finalize(c->counters, c->S, c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->lambda_d,
-                    c->eval_rec, c->ham_d, c->stream, c->w_d ? c->wvalue : nullptr);
+                    c->eval_rec, c->ham_d, c->stream,
+                    c->w_d ? c->wvalue : c->ew_d ? c->cutw : nullptr);
       c->launches += 2;
     }
   }
@@ -781,6 +795,25 @@ cpra_status check_err_flag(cpra_ctx* c) {
   return CPRA_OK;
 }
 
+// Edge weights: MaxCut only, finite, symmetric (A_ij = A_ji for the two CSR
+// entries of each edge; columns are sorted, so the reverse entry is found by
+// binary search).
+std::string validate_edge_weights(int64_t N, const int64_t* rowptr, const int32_t* col,
+                                  const float* w, int32_t problem) {
+  if (problem != CPRA_MAXCUT) return "edge weights apply to CPRA_MAXCUT only (w must be NULL)";
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      if (!std::isfinite(w[e])) return "edge weights must be finite";
+      const int32_t j = col[e];
+      const int32_t* b = col + rowptr[j];
+      const int32_t* f = col + rowptr[j + 1];
+      const int32_t* it = std::lower_bound(b, f, static_cast<int32_t>(i));
+      if (it == f || *it != i || w[rowptr[j] + (it - b)] != w[e])
+        return "edge weights must be symmetric (A_ij == A_ji)";
+    }
+  return std::string();
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -844,9 +877,12 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   };
   std::string msg = validate_config(cfg);
   if (!msg.empty()) { fail(c, CPRA_EINVAL, msg); return bail(CPRA_EINVAL); }
-  if (w != nullptr) { fail(c, CPRA_EINVAL, "edge weights are not supported (w must be NULL)"); return bail(CPRA_EINVAL); }
   msg = validate_graph(N, rowptr, col);
   if (!msg.empty()) { fail(c, CPRA_EINVAL, msg); return bail(CPRA_EINVAL); }
+  if (w != nullptr) {
+    msg = validate_edge_weights(N, rowptr, col, w, cfg->problem);
+    if (!msg.empty()) { fail(c, CPRA_EINVAL, msg); return bail(CPRA_EINVAL); }
+  }
   c->cfg = *cfg;
   c->num_sms = device_sm_count();
   set_dims(c, N, rowptr[N], cfg);
@@ -910,6 +946,34 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   if (s == CPRA_OK)
     s = cuda_check(c, cudaMemcpyAsync(c->lambda_d, c->lambda_h.data(), sizeof(float) * c->S, cudaMemcpyHostToDevice, st), "upload lambda");
   if (s != CPRA_OK) return bail(s);
+  std::vector<float> wdeg_h;
+  if (w != nullptr) {  // MaxCut edge weights, their weighted degrees (FP64 sums), cut partials
+    wdeg_h.assign((size_t)N, 0.f);
+    for (int64_t i = 0; i < N; ++i) {
+      double t = 0.0;
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) t += (double)w[e];
+      wdeg_h[i] = (float)t;
+    }
+    const size_t ew_b = (sizeof(float) * (size_t)c->nnz + 255) / 256 * 256;
+    const size_t wd_b = (sizeof(float) * (size_t)N + 255) / 256 * 256;
+    const size_t cp_b = sizeof(double) * (size_t)kWvBlocks * c->S;
+    cudaError_t e = cudaMalloc(&c->ew_mem, ew_b + wd_b + cp_b + sizeof(double) * c->S);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, CPRA_ENOMEM, std::string("cudaMalloc (edge weights): ") + cudaGetErrorString(e));
+      return bail(CPRA_ENOMEM);
+    }
+    char* b = static_cast<char*>(c->ew_mem);
+    c->ew_d = reinterpret_cast<float*>(b);
+    c->wdeg_d = reinterpret_cast<float*>(b + ew_b);
+    c->cut_part = reinterpret_cast<double*>(b + ew_b + wd_b);
+    c->cutw = c->cut_part + (size_t)kWvBlocks * c->S;
+    if (c->nnz > 0)
+      s = cuda_check(c, cudaMemcpyAsync(c->ew_d, w, sizeof(float) * c->nnz, cudaMemcpyHostToDevice, st), "upload w");
+    if (s == CPRA_OK)
+      s = cuda_check(c, cudaMemcpyAsync(c->wdeg_d, wdeg_h.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st), "upload weighted degrees");
+    if (s != CPRA_OK) return bail(s);
+  }
   // zero everything that must start at zero (pads included)
   const size_t act = act_bytes(c);
   cudaMemsetAsync(c->theta_m, 0, sizeof(float) * c->nparam, st);
@@ -1139,7 +1203,7 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
         const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
         // weighted MIS and DBM rank by value (weight, reward), the others by
         // the integer objective; objective -1 marks a shot with none yet
-        const bool by_value = c->wmis || c->cfg.problem == CPRA_DBM;
+        const bool by_value = c->wmis || c->cfg.problem == CPRA_DBM || c->ew_d != nullptr;
         const bool better = best_out[s].objective < 0 ||
                             (by_value ? cur[s].value > best_out[s].value
                                       : cur[s].objective > best_out[s].objective);
@@ -1425,6 +1489,7 @@ void cpra_destroy(cpra_ctx* c) {
   }
   drop_graph(c);
   if (c->dbm_mem) cudaFree(c->dbm_mem);
+  if (c->ew_mem) cudaFree(c->ew_mem);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -309,7 +309,43 @@ __global__ void weighted_value_finalize(int blocks, int S, const double* __restr
   value[s] = t;
 }
 
+// Weighted MaxCut: the cut weight of each shot, the sum of A_ij over the
+// edges j > i with x_is != x_js, in FP64.  Thread s of block b walks the rows
+// of b's range in order (the threads of a warp read the same column indices
+// and weights, and the same 32-shot bit words); the blocks are then added
+// in order by weighted_value_finalize.
+__global__ void weighted_cut_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
+                                    const int* __restrict__ col, const float* __restrict__ ew,
+                                    const uint32_t* __restrict__ bits, int64_t rows_per,
+                                    double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+  const int64_t r1 = r0 + rows_per < N ? r0 + rows_per : N;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int w = s >> 5, b = s & 31;
+    double t = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const uint32_t xr = (bits[r * W + w] >> b) & 1u;
+      for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const int j = col[e];
+        if (j > r && ((bits[(int64_t)j * W + w] >> b) & 1u) != xr) t += (double)ew[e];
+      }
+    }
+    part[(int64_t)blockIdx.x * S + s] = t;
+  }
+}
+
 }  // namespace
+
+void weighted_cut_launch(int64_t N, int S, const int* rowptr, const int* col, const float* ew,
+                         const uint32_t* bits, double* part, int max_blocks, double* value,
+                         cudaStream_t st) {
+  int64_t rows_per = (N + max_blocks - 1) / max_blocks;
+  if (rows_per < 1) rows_per = 1;
+  const int blocks = (int)((N + rows_per - 1) / rows_per);
+  weighted_cut_kernel<<<blocks, 128, 0, st>>>(N, S, (S + 31) / 32, rowptr, col, ew, bits,
+                                              rows_per, part);
+  weighted_value_finalize<<<(S + 127) / 128, 128, 0, st>>>(blocks, S, part, value);
+}
 
 void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* w, int64_t ldw,
                            double* part, int max_blocks, double* value, cudaStream_t st) {

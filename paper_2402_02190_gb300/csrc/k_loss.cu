@@ -19,7 +19,9 @@
 // evaluation of those bits runs in k_eval.cu.
 //
 // The epilogue is instantiated per problem: 0 MIS, 1 MaxCut, 2 DBM,
-// 3 weighted MIS (node weights w in place of the unit reward).
+// 3 weighted MIS (node weights w in place of the unit reward), 4 MaxCut with
+// edge weights A_ij (Q_i = sum_j A_ij P_j, and the weighted degree
+// sum_j A_ij in place of deg_i).
 //
 // Two kernels share the per-row epilogue:
 //   loss_kernel         rows of up to 64 shots (and bit packing alone):
@@ -322,13 +324,18 @@ loss_kernel(LossArgs a) {
     for (int eb = beg; eb < end; eb += LPR) {
       const int ee = eb + sub;
       const int jl = (ee < end) ? a.col[ee] : 0;
+      float wl = 1.f;  // edge weight A_ij (problem 4)
+      if constexpr (PROBLEM == 4) wl = (ee < end) ? a.ew[ee] : 0.f;
       const int cnt = min(LPR, end - eb);
       int k = 0;
       for (; k + 4 <= cnt; k += 4) {
         uint4 raw[4][CPL];
+        float wu[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = __shfl_sync(smask, jl, k + u, LPR);
+          wu[u] = 1.f;
+          if constexpr (PROBLEM == 4) wu[u] = __shfl_sync(smask, wl, k + u, LPR);
           const float* row = P + (int64_t)j * a.ldp;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
@@ -343,11 +350,16 @@ loss_kernel(LossArgs a) {
             float f[4];
             widen(raw[u][c], f, (const float*)nullptr);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) q[c][e] += f[e];
+            for (int e = 0; e < 4; ++e) {
+              if constexpr (PROBLEM == 4) q[c][e] = fmaf(wu[u], f[e], q[c][e]);
+              else q[c][e] += f[e];
+            }
           }
       }
       for (; k < cnt; ++k) {
         const int j = __shfl_sync(smask, jl, k, LPR);
+        float wk = 1.f;
+        if constexpr (PROBLEM == 4) wk = __shfl_sync(smask, wl, k, LPR);
         const float* row = P + (int64_t)j * a.ldp;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -356,13 +368,17 @@ loss_kernel(LossArgs a) {
             float f[4];
             widen(ldg_nc16(row + ch * 4), f, (const float*)nullptr);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) q[c][e] += f[e];
+            for (int e = 0; e < 4; ++e) {
+              if constexpr (PROBLEM == 4) q[c][e] = fmaf(wk, f[e], q[c][e]);
+              else q[c][e] += f[e];
+            }
           }
         }
       }
     }
-    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, gamma,
-                                        acc);
+    float deg = (float)(end - beg);
+    if constexpr (PROBLEM == 4) deg = a.wdeg[i];  // sum_j A_ij
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, deg, lam, gamma, acc);
   }
   if constexpr (DO_LOSS) block_reduce<LPR, CPL>(a, acc, red);
 }
@@ -500,6 +516,8 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
     const int beg = k ? sbeg1 : sbeg0;
     const int end = k ? send1 : send0;
     const int n = min(end - beg, CAP);
+    float wl = 1.f;  // weight of slot neighbour `lane` (problem 4), loaded before the wait
+    if constexpr (PROBLEM == 4) wl = (lane < n) ? a.ew[beg + lane] : 0.f;
     if (!ring_wait(bars + k, par)) {
       dead = true;
       break;
@@ -515,10 +533,18 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
     for (int t = 0; t < n; ++t) {
       float f[CPL][4];
       read_row(base + (size_t)(1 + t) * row_bytes, f);
+      if constexpr (PROBLEM == 4) {
+        const float wt = __shfl_sync(smask, wl, t);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c)
+        for (int c = 0; c < CPL; ++c)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) q[c][e] += f[c][e];
+          for (int e = 0; e < 4; ++e) q[c][e] = fmaf(wt, f[c][e], q[c][e]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) q[c][e] += f[c][e];
+      }
     }
     __syncwarp();
     issue_row(nxt, nbeg, nend, njl, k);  // refill the slot just read
@@ -540,6 +566,8 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
     }
     for (int e = beg + n; e < end; ++e) {  // neighbours beyond the slot capacity
       const float* row = P + (int64_t)a.col[e] * a.ldp;
+      float we = 1.f;
+      if constexpr (PROBLEM == 4) we = a.ew[e];
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int ch = c * LPR + sub;
@@ -547,13 +575,17 @@ loss_kernel_staged(LossArgs a, int CAP, int rslot_bytes, int bars_bytes) {
           float f[4];
           widen(ldg_nc16(row + ch * 4), f, (const float*)nullptr);
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) q[c][e2] += f[e2];
+          for (int e2 = 0; e2 < 4; ++e2) {
+            if constexpr (PROBLEM == 4) q[c][e2] = fmaf(we, f[e2], q[c][e2]);
+            else q[c][e2] += f[e2];
+          }
         }
       }
     }
     if (a.xbits) store_bits<LPR, CPL>(a, i, sub, smask, p);
-    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, (float)(end - beg), lam, gamma,
-                                        acc);
+    float deg = (float)(end - beg);
+    if constexpr (PROBLEM == 4) deg = a.wdeg[i];  // sum_j A_ij
+    row_epilogue<LPR, CPL, PROBLEM, TG>(a, i, sub, smask, p, q, deg, lam, gamma, acc);
   }
   if (dead) {
     if (lane == 0 && a.err_flag) atomicOr(a.err_flag, 2);
@@ -663,6 +695,10 @@ int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st) {
   if (a.problem == 2) {
     if (a.dg == DT_BF16) return dispatch_loss<2, bf16, true>(a, nch, max_grid, staged_grid, st);
     return dispatch_loss<2, float, true>(a, nch, max_grid, staged_grid, st);
+  }
+  if (a.ew) {  // MaxCut with edge weights
+    if (a.dg == DT_BF16) return dispatch_loss<4, bf16, true>(a, nch, max_grid, staged_grid, st);
+    return dispatch_loss<4, float, true>(a, nch, max_grid, staged_grid, st);
   }
   if (a.dg == DT_BF16) return dispatch_loss<1, bf16, true>(a, nch, max_grid, staged_grid, st);
   return dispatch_loss<1, float, true>(a, nch, max_grid, staged_grid, st);

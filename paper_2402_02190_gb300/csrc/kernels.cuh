@@ -137,6 +137,8 @@ struct LossArgs {
   const StepScalars* sc = nullptr;  // when set, gamma is sc->gamma
   const float* w = nullptr;   // weighted MIS (problem 0): node weights N x ldw, cost -sum w P
   int64_t ldw = 0;
+  const float* ew = nullptr;    // MaxCut (problem 1): edge weight per CSR entry, or null (unit)
+  const float* wdeg = nullptr;  //   and the weighted degree sum_j A_ij per node
   void* G = nullptr;             // dtype dg, N x ldg
   int dg = DT_F32;
   uint32_t* xbits = nullptr;     // N x W, W = ceil(S/32)
@@ -183,6 +185,11 @@ void eval_finalize(const unsigned long long* counters, int S, int problem,
 // fixed order.
 void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* w, int64_t ldw,
                            double* part, int max_blocks, double* value, cudaStream_t st);
+// Weighted MaxCut: value[s] = sum of A_ij over the edges j > i with
+// x_is != x_js (FP64, fixed order; part holds max_blocks x S partials).
+void weighted_cut_launch(int64_t N, int S, const int* rowptr, const int* col, const float* ew,
+                         const uint32_t* bits, double* part, int max_blocks, double* value,
+                         cudaStream_t st);
 
 // ---------------------------------------------------------------- DBM (k_dbm.cu)
 // Line sums of the relaxed matching P (FP32, N x ldp): R, K, T, U in the

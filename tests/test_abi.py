@@ -131,3 +131,34 @@ def test_memory_cap_fault_injection(L):
     st, msg = _init_status(rp, col, mem_cap_bytes=1024)
     assert st == cpra.CPRA_ENOMEM, msg
     assert "mem_cap_bytes" in msg
+
+
+def _init_weighted(rowptr, col, w, problem):
+    lam = np.ones(8, np.float32) if problem == cpra.MIS else None
+    cfg = cpra.make_config(problem=problem, S=8)
+    try:
+        cpra.cpra_init_graph(rowptr, col, cfg, lam=lam, workspace=None, weights=w)
+    except cpra.CpraError as e:
+        return e.status, str(e)
+    return cpra.CPRA_OK, ""
+
+
+@pytest.mark.parametrize("case", ["mis", "asym", "nan"])
+def test_invalid_edge_weights_rejected_on_host(L, case):
+    """Edge weights (the MaxCut QUBO's A_ij) are rejected before any device
+    work when they are given for another problem, differ between the two
+    CSR entries of an edge, or are not finite."""
+    rp, col = I.random_regular_graph(20, 3, seed=1)
+    w = I.seeded_edge_weights(rp, col, 2)
+    problem = cpra.MAXCUT
+    if case == "mis":
+        problem = cpra.MIS
+    elif case == "asym":
+        w = w.copy()
+        w[0] += 1.0
+    else:
+        w = w.copy()
+        w[3] = np.nan
+    st, msg = _init_weighted(rp, col, w, problem)
+    assert st == cpra.CPRA_EINVAL
+    assert {"mis": "CPRA_MAXCUT only", "asym": "symmetric", "nan": "finite"}[case] in msg

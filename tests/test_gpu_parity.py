@@ -231,13 +231,15 @@ STEP_CASES = [
 
 
 def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=None, plain=False,
-                   fp32_engine=0):
+                   fp32_engine=0, weights=None):
     """One GPU step from seeded state and the oracle's step from the same
     state.  With plain=True the BF16 form is also compared with the oracle
-    that decides the ReLU signs on FP64 Z1 (out["ref_plain"])."""
+    that decides the ReLU signs on FP64 Z1 (out["ref_plain"]).  ``weights``
+    ("uniform" or "pm1") gives a MaxCut case seeded edge weights A_ij."""
     problem, div, alpha, nu, S, H, N, gk = case
     rp, col = graph_of(gk, N, seed=N + S)
-    g = O.Graph(rp, col)
+    w = None if weights is None else I.seeded_edge_weights(rp, col, seed=S, kind=weights)
+    g = O.Graph(rp, col, weights=w)
     lam = I.lambda_geomspace(0.5, 10.0, S)
     theta, X0 = I.seeded_params(N, H, H, S, seed=5, weight_scale=1.5)
     mt, vt = I.seeded_adam_state(len(theta), seed=6)
@@ -247,7 +249,8 @@ def _run_step_case(case, precision, keep_emb_grad=1, recompute=0, init_logits=No
     solver = cpra.Solver(rp, col, lam=lam if problem == O.MIS else None, problem=problem, S=S,
                          H0=H, H1=H, alpha=alpha, precision=precision, nu=nu,
                          diversity_kind=div, gamma0=-1.0, gamma1=1.0, schedule_steps=T,
-                         keep_emb_grad=keep_emb_grad, recompute=recompute, fp32_engine=fp32_engine)
+                         keep_emb_grad=keep_emb_grad, recompute=recompute, fp32_engine=fp32_engine,
+                         weights=w)
     for which, arr in ((cpra.T_THETA, theta), (cpra.T_EMB, X0), (cpra.T_THETA_M, mt),
                        (cpra.T_THETA_V, vt), (cpra.T_EMB_M, mx), (cpra.T_EMB_V, vx),
                        (cpra.T_STEP, np.array([t_prev]))):
