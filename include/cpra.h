@@ -228,12 +228,27 @@ CPRA_API cpra_status cpra_round_eval(cpra_ctx* ctx, cpra_shot_eval* out,
    steps and after the last, tracks per shot the best evaluation: MIS the
    largest objective with violations == 0 (objective -1 if none seen),
    weighted MIS the largest value with violations == 0 (value -1 if none),
-   MaxCut the largest cut.  best_out: host [S]; best_step_out: host [S] step
+   MaxCut the largest cut (with edge weights, the largest cut weight).  best_out: host [S]; best_step_out: host [S] step
    index of that evaluation (or -1), may be NULL.  With es_patience > 0 the
    loop ends at the first evaluation after early stopping fired (the
    parameters are frozen from the stopping step on). */
 CPRA_API cpra_status cpra_solve(cpra_ctx* ctx, int64_t steps, int64_t eval_every,
                        cpra_shot_eval* best_out, int64_t* best_step_out);
+
+/* Metrics log (JSON Lines): with a path, cpra_solve appends one JSON object
+   per evaluation to that file, opened for appending:
+     {"t": step index evaluated, "gamma": gamma_t, "steps": steps since the
+      previous evaluation, "seconds": their wall time with this evaluation,
+      "elapsed": seconds since the cpra_solve call began, "psi": Psi,
+      "pair_hamming": sum_i k_i (S - k_i) of the rounded shots,
+      "cost" / "pen" / "ann": [S] loss terms of step t,
+      "objective" / "violations" / "value": [S] records of step t's rounding}
+   -- the quantities the paper's early stopping monitors (Implementation
+   paragraph) and the solution quality per evaluation.  Logging costs one
+   host copy of 3S+1 floats per evaluation.  path NULL closes the log; the
+   context closes it in cpra_destroy.  Errors: CPRA_EINVAL (the file cannot
+   be opened; cpra_solve returns it when a write fails). */
+CPRA_API cpra_status cpra_set_metrics_log(cpra_ctx* ctx, const char* path);
 
 /* Weighted MIS (problem CPRA_WMIS): node weights w [N x ld] float (ld >= S),
    w_is for node i in shot s, on the host (on_device = 0) or the current
@@ -367,7 +382,11 @@ CPRA_API void cpra_destroy(cpra_ctx* ctx);
  *       = -S^2 sum_i VAR_s(P_i.) (DIV_VAR)
  * (Eq. CPRA-loss-function-GNN-penalty / -variation, Table
  * objective-functions.)  Q is never stored.
- *   rowptr, col : device int32 [N+1], [nnz]
+ *   rowptr, col : device int32 [N+1], [nnz]: rowptr nondecreasing from 0
+ *                 to nnz, 0 <= col[e] < N.  These device arrays are not
+ *                 checked by the normal build (entries outside these bounds
+ *                 make the kernels read outside the arrays); the checked
+ *                 build tests them in the kernels (cpra_csr_check).
  *   P           : device float [N x ldp], ldp >= S, ldp % 4 == 0
  *   lambda      : device float [S] (MIS; ignored for MaxCut, may be NULL)
  *   grad_kind   : 0 -> G = dR/dP * P (1 - P)  (= dR/dZ2 under a sigmoid head)
@@ -406,6 +425,26 @@ CPRA_API cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* row
                                uint32_t* x_bits, cpra_shot_eval* out,
                                int64_t* pair_hamming, void* counters,
                                size_t counters_bytes, void* cuda_stream);
+
+/* Checked build.  libcpra_checked.so is this library compiled with
+ * CPRA_CHECKED: every kernel that walks the graph (the aggregations, the fused
+ * loss, the integer evaluation, the warm-start network's aggregations) tests
+ * each row range it reads against 0 <= rowptr[i] <= rowptr[i+1] <= rowptr[N]
+ * and each column index against 0 <= col[e] < N before using it.  A failing
+ * row is read as empty and a failing index as node 0, so no access leaves
+ * the arrays; the launch completes and its results are undefined.  There is
+ * no trap and no device assert: the failures are counted in device words.
+ * (The device CSR of a context was validated on the host by
+ * cpra_init_graph; the op-level calls and cpra_ws_* take device CSR arrays
+ * as given.)
+ * cpra_csr_check synchronises the device, returns the number of checks that
+ * failed since the previous call (a bad row or index is counted once for
+ * every lane and launch that reads it) and clears the words; *first_row
+ * receives the smallest row whose range failed and *first_entry the
+ * smallest CSR position whose column index failed (-1 for none; either
+ * pointer may be NULL).  -2 if the synchronisation reports a CUDA error.
+ * The normal build returns -1 and writes -1. */
+CPRA_API int64_t cpra_csr_check(int64_t* first_row, int64_t* first_entry);
 
 /* Allocation-free variant of cpra_op_loss.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code

@@ -18,6 +18,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libcpra.so")
+# the checked build: in-kernel CSR bound checks, read through cpra_csr_check
+LIB_CHECKED_PATH = os.path.join(_HERE, "lib", "libcpra_checked.so")
+_LIB_PATHS = {"release": LIB_PATH, "checked": LIB_CHECKED_PATH}
 
 CPRA_OK, CPRA_EINVAL, CPRA_ENOMEM, CPRA_ECUDA, CPRA_ENUMERIC, CPRA_ETIMEOUT, CPRA_ESTATE = range(7)
 MIS, MAXCUT, WMIS, DBM = 0, 1, 2, 3
@@ -38,7 +41,7 @@ ABI_FUNCTIONS = (
     "cpra_set_init_logits", "cpra_steps", "cpra_set_node_weights", "cpra_set_dbm",
     "cpra_inject_error_flag", "cpra_ws_config_default", "cpra_ws_param_count", "cpra_ws_create",
     "cpra_ws_features", "cpra_ws_train_step", "cpra_ws_predict", "cpra_ws_get_params",
-    "cpra_ws_set_params", "cpra_ws_destroy",
+    "cpra_ws_set_params", "cpra_ws_destroy", "cpra_csr_check", "cpra_set_metrics_log",
 )
 NOALLOC_MAX_S = 1024
 
@@ -79,18 +82,31 @@ class ShotEval(C.Structure):
 SHOT_EVAL_DTYPE = np.dtype([("objective", "<i8"), ("violations", "<i8"), ("qubo", "<f8"),
                             ("value", "<f8")])
 
-_lib = None
+_libs = {}
+_variant = os.environ.get("CPRA_LIBRARY", "release")
+
+
+def use_library(variant: str) -> str:
+    """Selects the library the module-level calls go to: "release"
+    (libcpra.so) or "checked" (libcpra_checked.so).  Returns the previous
+    choice.  A context belongs to the library that created it: switch only
+    between contexts, never with one open."""
+    global _variant
+    if variant not in _LIB_PATHS:
+        raise ValueError(f"unknown library variant {variant!r}")
+    prev, _variant = _variant, variant
+    return prev
 
 
 def lib():
-    """Loads libcpra.so (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
+    """Loads the selected library (raises if it has not been built)."""
+    if _variant in _libs:
+        return _libs[_variant]
+    path = _LIB_PATHS[_variant]
+    if not os.path.exists(path):
         raise ImportError(
-            f"{LIB_PATH} is missing: build it with paper_2402_02190_gb300.build.build()")
-    L = C.CDLL(LIB_PATH)
+            f"{path} is missing: build it with paper_2402_02190_gb300.build.build()")
+    L = C.CDLL(path)
     vp, i32, i64, f32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_size_t
     P_cfg = C.POINTER(Config)
     sigs = {
@@ -137,6 +153,8 @@ def lib():
                                    vp, i64, vp, vp, vp, sz, vp]),
         "cpra_op_loss_noalloc": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, i32, f32, f32,
                                            i32, i32, vp, i64, vp, vp, vp]),
+        "cpra_csr_check": (i64, [vp, vp]),
+        "cpra_set_metrics_log": (i32, [vp, C.c_char_p]),
         "cpra_op_round_eval_scratch_bytes": (sz, [i32]),
         "cpra_op_round_eval": (C.c_int, [i64, i32, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, sz,
                                          vp]),
@@ -145,8 +163,16 @@ def lib():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    _lib = L
+    _libs[_variant] = L
     return L
+
+
+def cpra_csr_check():
+    """(failed checks since the last call, smallest bad row, smallest bad CSR
+    position) from the checked build; (-1, -1, -1) from the release build."""
+    row, ent = C.c_int64(-1), C.c_int64(-1)
+    n = lib().cpra_csr_check(C.byref(row), C.byref(ent))
+    return int(n), int(row.value), int(ent.value)
 
 
 def _check(status: int, ctx=None):
@@ -479,6 +505,12 @@ class Solver:
 
     def solve(self, steps: int, eval_every: int):
         return cpra_solve(self.ctx, steps, eval_every)
+
+    def set_metrics_log(self, path) -> None:
+        """cpra_solve appends one JSON line per evaluation to `path` (None
+        closes the log)."""
+        _check(lib().cpra_set_metrics_log(
+            self.ctx, None if path is None else os.fsencode(path)), self.ctx)
 
     def set_node_weights(self, w) -> None:
         if hasattr(w, "is_cuda") and w.is_cuda:

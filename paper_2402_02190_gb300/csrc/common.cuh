@@ -242,4 +242,74 @@ __device__ __forceinline__ unsigned segment_mask(int lane) {
   }
 }
 
+// ------------------------------------------------------------------ CSR reads
+// Every kernel that walks the graph reads its CSR through csr_row and
+// csr_col.  The normal build loads what it is given (cpra_init_graph checks
+// the graph on the host; the op-level calls document their contract).  The
+// checked build (CPRA_CHECKED) tests each row range against
+// 0 <= rowptr[i] <= rowptr[i+1] <= rowptr[N] and each column index against
+// 0 <= col[e] < N before it is used: a failing row is read as empty and a
+// failing index as node 0, so no access leaves the arrays, and the failure is
+// counted in this translation unit's device words, which the host reads and
+// clears through the translation unit's collector (CPRA_CSR_CHECK_COLLECT).
+#ifdef CPRA_CHECKED
+namespace {
+__device__ unsigned long long g_csr_fail_count = 0;
+__device__ long long g_csr_fail_row = 0x7fffffffffffffffLL;    // smallest bad row range
+__device__ long long g_csr_fail_entry = 0x7fffffffffffffffLL;  // smallest bad column position
+}  // namespace
+#endif
+
+__device__ __forceinline__ void csr_row(const int* rowptr, int64_t i, int64_t N, int& beg,
+                                        int& end) {
+  beg = rowptr[i];
+  end = rowptr[i + 1];
+#ifdef CPRA_CHECKED
+  const int nnz = rowptr[N];
+  if (!(0 <= beg && beg <= end && end <= nnz)) {
+    atomicAdd(&g_csr_fail_count, 1ull);
+    atomicMin(&g_csr_fail_row, (long long)i);
+    beg = end = 0;
+  }
+#else
+  (void)N;
+#endif
+}
+
+__device__ __forceinline__ int csr_col(const int* col, int64_t e, int64_t N) {
+  const int j = col[e];
+#ifdef CPRA_CHECKED
+  if (j < 0 || (int64_t)j >= N) {
+    atomicAdd(&g_csr_fail_count, 1ull);
+    atomicMin(&g_csr_fail_entry, (long long)e);
+    return 0;
+  }
+#else
+  (void)N;
+#endif
+  return j;
+}
+
 }  // namespace cpra
+
+#ifdef CPRA_CHECKED
+// Body of a translation unit's collector: adds its failure count into the
+// CsrCheck *r, lowers r's smallest bad row and position, and clears the
+// device words.  The caller synchronises the device first.
+#define CPRA_CSR_CHECK_COLLECT(r)                                                         \
+  do {                                                                                    \
+    unsigned long long n_ = 0;                                                            \
+    long long row_ = 0, ent_ = 0;                                                         \
+    cudaMemcpyFromSymbol(&n_, g_csr_fail_count, sizeof(n_));                              \
+    cudaMemcpyFromSymbol(&row_, g_csr_fail_row, sizeof(row_));                            \
+    cudaMemcpyFromSymbol(&ent_, g_csr_fail_entry, sizeof(ent_));                          \
+    (r)->count += n_;                                                                     \
+    if (row_ < (r)->first_row) (r)->first_row = row_;                                     \
+    if (ent_ < (r)->first_entry) (r)->first_entry = ent_;                                 \
+    const unsigned long long zero_ = 0;                                                   \
+    const long long none_ = 0x7fffffffffffffffLL;                                         \
+    cudaMemcpyToSymbol(g_csr_fail_count, &zero_, sizeof(zero_));                          \
+    cudaMemcpyToSymbol(g_csr_fail_row, &none_, sizeof(none_));                            \
+    cudaMemcpyToSymbol(g_csr_fail_entry, &none_, sizeof(none_));                          \
+  } while (0)
+#endif

@@ -13,11 +13,14 @@
 //             GEMM  [G_X0a | G_M1/deg] = G_Z1 Wcat1;  SPMM dX0 = G_X0a + A G_M1/deg
 //   update    Adam on theta (+ BF16 weight shadows), Adam on the embeddings
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "cpra.h"
 #include "kernels.cuh"
@@ -132,6 +135,8 @@ struct cpra_ctx {
   float* wdeg_d = nullptr;
   double* cut_part = nullptr;
   double* cutw = nullptr;
+  // JSON-lines metrics log written by cpra_solve (cpra_set_metrics_log)
+  FILE* metrics = nullptr;
   DbmDev dbm;                     // matching instances (problem DBM)
   void* dbm_mem = nullptr;        // own cudaMalloc behind dbm, null until cpra_set_dbm
   int64_t dbm_bytes = 0;
@@ -377,11 +382,37 @@ void set_dims(cpra_ctx* c, int64_t N, int64_t nnz, const cpra_config* cfg) {
 }
 
 // ---------------------------------------------------------------- profiling
+// NVTX ranges in the "cpra" domain: one per ABI call that launches work and
+// one per kernel region of a step (named as cpra_kernel_name names them), so
+// that a timeline profiler shows the step's structure.  Without a profiler
+// attached a range costs an indirect call.  A captured step (cpra_steps)
+// opens its kernel ranges once, while it is captured, not on each replay.
+nvtxDomainHandle_t nvtx_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("cpra");
+  return d;
+}
+
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+    nvtxEventAttributes_t a;
+    std::memset(&a, 0, sizeof(a));
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+  }
+  ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Region {
+  NvtxRange range;
   cpra_ctx* c;
   int id;
   size_t slot = (size_t)-1;
-  Region(cpra_ctx* ctx, int kid) : c(ctx), id(kid) {
+  Region(cpra_ctx* ctx, int kid) : range(kKernelNames[kid]), c(ctx), id(kid) {
     if (!c->prof || c->capturing) return;
     if (c->prof_used == c->prof_ring.size()) {
       // flush: synchronise and accumulate
@@ -403,6 +434,45 @@ struct Region {
     if (slot != (size_t)-1) cudaEventRecord(c->prof_ring[slot].b, c->stream);
   }
 };
+
+float gamma_at(const cpra_config& cfg, int64_t t);
+
+// One JSON line of the metrics log per evaluation: the step index t, gamma_t,
+// the steps since the previous evaluation and their wall time (with this
+// evaluation), the time since the solve began, the step's loss terms per
+// shot and Psi, the rounded shots' objective, violations and value, and
+// sum_i k_i (S - k_i).
+cpra_status write_metrics(cpra_ctx* c, int64_t t, int64_t n_steps, double seconds, double elapsed,
+                          const cpra_shot_eval* rec, int64_t ham) {
+  const int S = c->S;
+  std::vector<float> terms(3 * (size_t)S + 1);
+  cpra_status st = cuda_check(c, cudaMemcpyAsync(terms.data(), c->terms, sizeof(float) * terms.size(),
+                                                 cudaMemcpyDeviceToHost, c->stream),
+                              "metrics terms readback");
+  if (st == CPRA_OK) st = cuda_check(c, cudaStreamSynchronize(c->stream), "metrics sync");
+  if (st != CPRA_OK) return st;
+  FILE* f = c->metrics;
+  std::fprintf(f, "{\"t\": %lld, \"gamma\": %.9g, \"steps\": %lld, \"seconds\": %.6f, "
+               "\"elapsed\": %.6f, \"psi\": %.9g, \"pair_hamming\": %lld",
+               (long long)t, (double)gamma_at(c->cfg, t), (long long)n_steps, seconds, elapsed,
+               (double)terms[3 * (size_t)S], (long long)ham);
+  const char* names[3] = {"cost", "pen", "ann"};
+  for (int k = 0; k < 3; ++k) {
+    std::fprintf(f, ", \"%s\": [", names[k]);
+    for (int s = 0; s < S; ++s)
+      std::fprintf(f, s ? ", %.9g" : "%.9g", (double)terms[(size_t)k * S + s]);
+    std::fputc(']', f);
+  }
+  std::fputs(", \"objective\": [", f);
+  for (int s = 0; s < S; ++s) std::fprintf(f, s ? ", %lld" : "%lld", (long long)rec[s].objective);
+  std::fputs("], \"violations\": [", f);
+  for (int s = 0; s < S; ++s) std::fprintf(f, s ? ", %lld" : "%lld", (long long)rec[s].violations);
+  std::fputs("], \"value\": [", f);
+  for (int s = 0; s < S; ++s) std::fprintf(f, s ? ", %.17g" : "%.17g", rec[s].value);
+  std::fputs("]}\n", f);
+  if (std::fflush(f) != 0 || std::ferror(f)) return fail(c, CPRA_EINVAL, "metrics log write failed");
+  return CPRA_OK;
+}
 
 void refresh_shadows(cpra_ctx* c) {
   if (c->act_dt == DT_BF16) {
@@ -1079,6 +1149,7 @@ cpra_status capture_step(cpra_ctx* c) {
 }  // namespace
 
 cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
+  NvtxRange range("cpra_step");
   if (!c) return CPRA_EINVAL;
   c->fwd_valid = false;
   launch_step_scalars(c, false, t);
@@ -1099,6 +1170,7 @@ cpra_status cpra_step(cpra_ctx* c, int64_t t, float* loss_terms_out) {
 }
 
 cpra_status cpra_steps(cpra_ctx* c, int64_t t0, int64_t n) {
+  NvtxRange range("cpra_steps");
   if (!c || n < 0) return c ? fail(c, CPRA_EINVAL, "cpra_steps: n < 0") : CPRA_EINVAL;
   if (n == 0) return CPRA_OK;
   // the first step runs directly: it sets the device counters to (t0 + 1,
@@ -1121,6 +1193,7 @@ cpra_status cpra_steps(cpra_ctx* c, int64_t t0, int64_t n) {
 }
 cpra_status cpra_forward(cpra_ctx* c, const float* theta_dev, const float* emb_dev, float gamma,
                          float* terms_dev) {
+  NvtxRange range("cpra_forward");
   if (!c || !theta_dev || !emb_dev || !terms_dev)
     return c ? fail(c, CPRA_EINVAL, "cpra_forward: NULL pointer") : CPRA_EINVAL;
   if (!std::isfinite(gamma)) return fail(c, CPRA_EINVAL, "cpra_forward: gamma must be finite");
@@ -1143,6 +1216,7 @@ cpra_status cpra_forward(cpra_ctx* c, const float* theta_dev, const float* emb_d
 }
 
 cpra_status cpra_backward(cpra_ctx* c, float scale, float* grad_theta_dev, float* grad_emb_dev) {
+  NvtxRange range("cpra_backward");
   if (!c || !grad_theta_dev) return c ? fail(c, CPRA_EINVAL, "cpra_backward: NULL pointer") : CPRA_EINVAL;
   if (!c->fwd_valid) return fail(c, CPRA_ESTATE, "cpra_backward: no cpra_forward to differentiate");
   cpra_status s = run_backward(c, grad_emb_dev != nullptr);
@@ -1158,6 +1232,7 @@ cpra_status cpra_backward(cpra_ctx* c, float scale, float* grad_theta_dev, float
 
 cpra_status cpra_round_eval(cpra_ctx* c, cpra_shot_eval* out, int64_t* pair_hamming_sum,
                             uint32_t* x_bits_out) {
+  NvtxRange range("cpra_round_eval");
   if (!c || !out) return c ? fail(c, CPRA_EINVAL, "out is NULL") : CPRA_EINVAL;
   if (!c->have_eval) {
     cpra_status s = run_forward_and_loss(c, gamma_at(c->cfg, 0), false);
@@ -1176,10 +1251,24 @@ cpra_status cpra_round_eval(cpra_ctx* c, cpra_shot_eval* out, int64_t* pair_hamm
   return s;
 }
 
+cpra_status cpra_set_metrics_log(cpra_ctx* c, const char* path) {
+  if (!c) return CPRA_EINVAL;
+  if (c->metrics) std::fclose(c->metrics);
+  c->metrics = nullptr;
+  if (!path) return CPRA_OK;
+  c->metrics = std::fopen(path, "a");
+  if (!c->metrics) return fail(c, CPRA_EINVAL, std::string("cannot open metrics log ") + path);
+  return CPRA_OK;
+}
+
 cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot_eval* best_out,
                        int64_t* best_step_out) {
+  NvtxRange range("cpra_solve");
   if (!c || !best_out || steps < 1) return c ? fail(c, CPRA_EINVAL, "bad solve arguments") : CPRA_EINVAL;
   if (eval_every < 1) eval_every = steps;
+  using Clock = std::chrono::steady_clock;
+  const Clock::time_point t_begin = Clock::now();
+  Clock::time_point t_last = t_begin;
   std::vector<cpra_shot_eval> cur((size_t)c->S);
   std::vector<int64_t> best_step((size_t)c->S, -1);
   for (int s = 0; s < c->S; ++s) {
@@ -1191,14 +1280,23 @@ cpra_status cpra_solve(cpra_ctx* c, int64_t steps, int64_t eval_every, cpra_shot
   for (int64_t t = 0; t < steps;) {
     // steps t .. t_eval in one call (a captured step replayed), then evaluate
     int64_t t_eval = (t == 0) ? 0 : std::min(steps - 1, (t + eval_every - 1) / eval_every * eval_every);
-    cpra_status st = cpra_steps(c, t, t_eval - t + 1);
+    const int64_t n_steps = t_eval - t + 1;
+    cpra_status st = cpra_steps(c, t, n_steps);
     if (st != CPRA_OK) return st;
     t = t_eval + 1;
     {
-      st = cpra_round_eval(c, cur.data(), nullptr, nullptr);
+      int64_t ham = 0;
+      st = cpra_round_eval(c, cur.data(), c->metrics ? &ham : nullptr, nullptr);
       if (st != CPRA_OK) return st;
       st = check_err_flag(c);
       if (st != CPRA_OK) return st;
+      if (c->metrics) {
+        const Clock::time_point now = Clock::now();
+        st = write_metrics(c, t_eval, n_steps, std::chrono::duration<double>(now - t_last).count(),
+                           std::chrono::duration<double>(now - t_begin).count(), cur.data(), ham);
+        if (st != CPRA_OK) return st;
+        t_last = Clock::now();
+      }
       for (int s = 0; s < c->S; ++s) {
         const bool ok = c->cfg.problem == CPRA_MAXCUT || cur[s].violations == 0;
         // weighted MIS and DBM rank by value (weight, reward), the others by
@@ -1490,6 +1588,7 @@ void cpra_destroy(cpra_ctx* c) {
   drop_graph(c);
   if (c->dbm_mem) cudaFree(c->dbm_mem);
   if (c->ew_mem) cudaFree(c->ew_mem);
+  if (c->metrics) std::fclose(c->metrics);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->init_logits) cudaFree(c->init_logits);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1704,6 +1803,7 @@ cpra_status cpra_op_loss(int64_t N, int32_t S, const int32_t* rowptr, const int3
                          int32_t alpha, float gamma, float nu, int32_t diversity_kind,
                          int32_t grad_kind, float* G, int64_t ldg, uint32_t* x_bits,
                          float* terms, void* scratch, size_t scratch_bytes, void* cuda_stream) {
+  NvtxRange range("cpra_op_loss");
   if (N < 1 || S < 1 || S > 1024 || !rowptr || !col || !P || !G || !terms || !scratch)
     return CPRA_EINVAL;
   if (ldp < S || ldp % 4 || ldg < S || ldg % 4 || ldg > round_up(S, 16)) return CPRA_EINVAL;
@@ -1735,6 +1835,7 @@ cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr, cons
                                const float* P, int64_t ldp, const float* lambda, int32_t problem,
                                uint32_t* x_bits, cpra_shot_eval* out, int64_t* pair_hamming,
                                void* counters, size_t counters_bytes, void* cuda_stream) {
+  NvtxRange range("cpra_op_round_eval");
   if (N < 1 || S < 1 || S > 1024 || !rowptr || !col || !P || !x_bits || !out || !pair_hamming ||
       !counters)
     return CPRA_EINVAL;
@@ -1755,6 +1856,27 @@ cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr, cons
   eval_bits_launch(N, S, rowptr, col, x_bits, problem, cnt, sms * 8, st);
   eval_finalize(cnt, S, problem, lambda, out, reinterpret_cast<long long*>(pair_hamming), st);
   return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
+}
+
+int64_t cpra_csr_check(int64_t* first_row, int64_t* first_entry) {
+  if (first_row) *first_row = -1;
+  if (first_entry) *first_entry = -1;
+#ifdef CPRA_CHECKED
+  if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+  CsrCheck r;
+  csr_check_collect_spmm(&r);
+  csr_check_collect_eval(&r);
+  csr_check_collect_loss<0>(&r);
+  csr_check_collect_loss<1>(&r);
+  csr_check_collect_loss<2>(&r);
+  csr_check_collect_loss<3>(&r);
+  csr_check_collect_loss<4>(&r);
+  if (first_row && r.first_row != CsrCheck().first_row) *first_row = r.first_row;
+  if (first_entry && r.first_entry != CsrCheck().first_entry) *first_entry = r.first_entry;
+  return (int64_t)r.count;
+#else
+  return -1;
+#endif
 }
 
 }  // extern "C"

@@ -194,14 +194,12 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
   // the next row's range, are loaded one row ahead
   int beg = 0, end = 0, jfirst = -1, nbeg = 0, nend = 0;
   if (first < N) {
-    beg = rowptr[first];
-    end = rowptr[first + 1];
+    csr_row(rowptr, first, N, beg, end);
     if constexpr (PROBLEM == 2) end = beg;  // set sizes and the Hamming sum only
-    jfirst = (sub < end - beg) ? col[beg + sub] : -1;
+    jfirst = (sub < end - beg) ? csr_col(col, beg + sub, N) : -1;
   }
   if (first + stride < N) {
-    nbeg = rowptr[first + stride];
-    nend = rowptr[first + stride + 1];
+    csr_row(rowptr, first + stride, N, nbeg, nend);
     if constexpr (PROBLEM == 2) nend = nbeg;
   }
   // rows in step across the warp: a segment whose rows are done runs the
@@ -209,11 +207,10 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
   for (int64_t i = first; __any_sync(0xffffffffu, i < N); i += stride) {
     const bool row = i < N;
     const uint32_t xi = (row && active) ? bits[i * W + sub] : 0u;
-    const int njfirst = (i + stride < N && sub < nend - nbeg) ? col[nbeg + sub] : -1;
+    const int njfirst = (i + stride < N && sub < nend - nbeg) ? csr_col(col, nbeg + sub, N) : -1;
     int pbeg = 0, pend = 0;
     if (i + 2 * stride < N) {
-      pbeg = rowptr[i + 2 * stride];
-      pend = rowptr[i + 2 * stride + 1];
+      csr_row(rowptr, i + 2 * stride, N, pbeg, pend);
       if constexpr (PROBLEM == 2) pend = pbeg;
     }
     // Neighbour passes of L column indices, in step across the warp (every
@@ -221,7 +218,7 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
     // are warp-uniform; a segment past its row's end contributes nothing).
     for (int eb = beg;; eb += L) {
       if (!__any_sync(0xffffffffu, eb < end)) break;
-      const int j = (eb == beg) ? jfirst : ((eb + sub < end) ? col[eb + sub] : -1);
+      const int j = (eb == beg) ? jfirst : ((eb + sub < end) ? csr_col(col, eb + sub, N) : -1);
       // the segment's neighbours j > i, as a mask over its lanes
       uint32_t m = __ballot_sync(0xffffffffu, j > i) >> (seg * L);
       if constexpr (L < 32) m &= (1u << (L & 31)) - 1u;
@@ -325,8 +322,10 @@ __global__ void weighted_cut_kernel(int64_t N, int S, int W, const int* __restri
     double t = 0.0;
     for (int64_t r = r0; r < r1; ++r) {
       const uint32_t xr = (bits[r * W + w] >> b) & 1u;
-      for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
-        const int j = col[e];
+      int beg, end;
+      csr_row(rowptr, r, N, beg, end);
+      for (int e = beg; e < end; ++e) {
+        const int j = csr_col(col, e, N);
         if (j > r && ((bits[(int64_t)j * W + w] >> b) & 1u) != xr) t += (double)ew[e];
       }
     }
@@ -363,5 +362,9 @@ void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const
   else if (W <= 16) launch_l<16>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
   else launch_l<32>(N, S, W, rowptr, col, bits, problem, counters, max_grid, st);
 }
+
+#ifdef CPRA_CHECKED
+void csr_check_collect_eval(CsrCheck* r) { CPRA_CSR_CHECK_COLLECT(r); }
+#endif
 
 }  // namespace cpra

@@ -3,10 +3,20 @@
 // not take.  128 x 128 output tile per block, 16 x 16 threads with 8 x 8
 // outputs each, K staged through double-buffered shared memory in slices of
 // 16.  Operands may be K-major or MN-major, FP32 or BF16.
+//
+// The build compiles this file once per operand type pair, with
+// -DCPRA_SIMT_DA=<DType of A> -DCPRA_SIMT_DB=<DType of B>, so that the four
+// sets of kernel instances (each with its four operand layouts) compile in
+// parallel; the (FP32, FP32) object also holds the host dispatch and the
+// split-K reduction.
 #include <math.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
+
+#if !defined(CPRA_SIMT_DA) || !defined(CPRA_SIMT_DB)
+#error "k_gemm_simt.cu is compiled with -DCPRA_SIMT_DA=<0|1> -DCPRA_SIMT_DB=<0|1>"
+#endif
 
 namespace cpra {
 
@@ -260,15 +270,25 @@ void launch_layout(const GemmArgs& g, dim3 grid, cudaStream_t st) {
   }
 }
 
+template <int D> struct SimtType { using T = float; };
+template <> struct SimtType<DT_BF16> { using T = bf16; };
+
+template <>
+void gemm_simt_launch_typed<CPRA_SIMT_DA, CPRA_SIMT_DB>(const GemmArgs& g, dim3 grid,
+                                                        cudaStream_t st) {
+  launch_layout<SimtType<CPRA_SIMT_DA>::T, SimtType<CPRA_SIMT_DB>::T>(g, grid, st);
+}
+
+#if CPRA_SIMT_DA == DT_F32 && CPRA_SIMT_DB == DT_F32
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st) {
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.Nc + BN - 1) / BN),
             g.epi == EPI_PARTIAL ? (unsigned)g.splits : 1u);
   if (g.da == DT_BF16) {
-    if (g.db == DT_BF16) launch_layout<bf16, bf16>(g, grid, st);
-    else launch_layout<bf16, float>(g, grid, st);
+    if (g.db == DT_BF16) gemm_simt_launch_typed<DT_BF16, DT_BF16>(g, grid, st);
+    else gemm_simt_launch_typed<DT_BF16, DT_F32>(g, grid, st);
   } else {
-    if (g.db == DT_BF16) launch_layout<float, bf16>(g, grid, st);
-    else launch_layout<float, float>(g, grid, st);
+    if (g.db == DT_BF16) gemm_simt_launch_typed<DT_F32, DT_BF16>(g, grid, st);
+    else gemm_simt_launch_typed<DT_F32, DT_F32>(g, grid, st);
   }
 }
 
@@ -278,5 +298,6 @@ void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp, fl
   splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, splits, M, Nc, ldp,
                                                                      out, ldo);
 }
+#endif
 
 }  // namespace cpra

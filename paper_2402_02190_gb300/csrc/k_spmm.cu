@@ -95,21 +95,15 @@ spmm_rows_kernel(SpmmArgs a) {
   const bool lines = a.line_r != nullptr;
   int beg = 0, end = 0, jl = 0, pbeg = 0, pend = 0;
   if (!lines && first < a.N) {
-    beg = a.rowptr[first];
-    end = a.rowptr[first + 1];
-    jl = (sub < end - beg) ? a.col[beg + sub] : 0;
+    csr_row(a.rowptr, first, a.N, beg, end);
+    jl = (sub < end - beg) ? csr_col(a.col, beg + sub, a.N) : 0;
   }
-  if (!lines && first + stride < a.N) {
-    pbeg = a.rowptr[first + stride];
-    pend = a.rowptr[first + stride + 1];
-  }
+  if (!lines && first + stride < a.N) csr_row(a.rowptr, first + stride, a.N, pbeg, pend);
   for (int64_t i = first; i < a.N; i += stride) {
-    const int njl = (!lines && i + stride < a.N && sub < pend - pbeg) ? a.col[pbeg + sub] : 0;
+    const int njl =
+        (!lines && i + stride < a.N && sub < pend - pbeg) ? csr_col(a.col, pbeg + sub, a.N) : 0;
     int ppbeg = 0, ppend = 0;
-    if (!lines && i + 2 * stride < a.N) {
-      ppbeg = a.rowptr[i + 2 * stride];
-      ppend = a.rowptr[i + 2 * stride + 1];
-    }
+    if (!lines && i + 2 * stride < a.N) csr_row(a.rowptr, i + 2 * stride, a.N, ppbeg, ppend);
     // the row's own operands first, so that they arrive with the gathers
     uint4 rad[CPL], rmk[CPL];
     uint32_t mbits[CPL];
@@ -157,7 +151,7 @@ spmm_rows_kernel(SpmmArgs a) {
     }
     for (int eb = beg; eb < end; eb += LPR) {
       const int e = eb + sub;
-      const int jc = (eb == beg) ? jl : ((e < end) ? a.col[e] : 0);
+      const int jc = (eb == beg) ? jl : ((e < end) ? csr_col(a.col, e, a.N) : 0);
       const int cnt = min(LPR, end - eb);
       int k = 0;
       for (; k + 4 <= cnt; k += 4) {
@@ -395,5 +389,9 @@ int spmm_launch(const SpmmArgs& a0, int num_sms, int max_grid, cudaStream_t st) 
   if (nsl > 1) a.H = 16 * ((a.H / 16 + nsl - 1) / nsl);
   return spmm_launch_one(a, num_sms, max_grid, st);
 }
+
+#ifdef CPRA_CHECKED
+void csr_check_collect_spmm(CsrCheck* r) { CPRA_CSR_CHECK_COLLECT(r); }
+#endif
 
 }  // namespace cpra

@@ -152,6 +152,18 @@ int64_t loss_pstride(int S);
 constexpr int kLossMaxGrid = 2048;
 // Returns the grid size used (row count of partials).
 int loss_launch(const LossArgs& a, int max_grid, cudaStream_t st);
+// The loss kernels' instances for one problem (0 MIS, 1 MaxCut, 2 DBM,
+// 3 weighted MIS, 4 MaxCut with edge weights), each compiled in its own
+// object from k_loss_problem.cu; nch = ldg / 4.  loss_launch_bits (in the
+// problem-0 object) packs the rounding bits alone, nch = ceil(S / 4).
+template <int PROBLEM>
+int loss_launch_problem(const LossArgs& a, int nch, int max_grid, int staged_grid, cudaStream_t st);
+template <> int loss_launch_problem<0>(const LossArgs&, int, int, int, cudaStream_t);
+template <> int loss_launch_problem<1>(const LossArgs&, int, int, int, cudaStream_t);
+template <> int loss_launch_problem<2>(const LossArgs&, int, int, int, cudaStream_t);
+template <> int loss_launch_problem<3>(const LossArgs&, int, int, int, cudaStream_t);
+template <> int loss_launch_problem<4>(const LossArgs&, int, int, int, cudaStream_t);
+int loss_launch_bits(const LossArgs& a, int nch, int max_grid, cudaStream_t st);
 
 // Sum partial rows: out[c] = sum_{b < nblocks} part[b*pstride + c], c < ncols,
 // in a fixed order; also copies out[copy_from .. copy_from+copy_n) to out2
@@ -258,6 +270,13 @@ struct GemmArgs {
   int d_add = DT_F32;
 };
 void gemm_simt_launch(const GemmArgs& g, cudaStream_t st);
+// gemm_simt_launch's instances for one (A, B) DType pair, each compiled in
+// its own object; grid = (M tiles, Nc tiles, splits).
+template <int DA, int DB> void gemm_simt_launch_typed(const GemmArgs& g, dim3 grid, cudaStream_t st);
+template <> void gemm_simt_launch_typed<DT_F32, DT_F32>(const GemmArgs&, dim3, cudaStream_t);
+template <> void gemm_simt_launch_typed<DT_F32, DT_BF16>(const GemmArgs&, dim3, cudaStream_t);
+template <> void gemm_simt_launch_typed<DT_BF16, DT_F32>(const GemmArgs&, dim3, cudaStream_t);
+template <> void gemm_simt_launch_typed<DT_BF16, DT_BF16>(const GemmArgs&, dim3, cudaStream_t);
 // out[r*ldo + c] = sum_z part[z*M*ldp + r*ldp + c] for r < M, c < Nc.
 void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp,
                    float* out, int64_t ldo, cudaStream_t st);
@@ -343,5 +362,25 @@ void total_loss_launch(const float* terms, const float* lambda, int S, float gam
                        float* out, cudaStream_t st);
 // dst[i] = scale * src[i]
 void scale_copy_launch(int64_t n, float scale, const float* src, float* dst, cudaStream_t st);
+
+// Failures of the in-kernel CSR checks of the checked build (csr_row /
+// csr_col in common.cuh): how many checks failed (a bad row or index counts
+// once per lane and launch that reads it), the smallest row with a bad range
+// and the smallest CSR position with a bad column index (INT64_MAX if none).
+struct CsrCheck {
+  unsigned long long count = 0;
+  long long first_row = 0x7fffffffffffffffLL;
+  long long first_entry = 0x7fffffffffffffffLL;
+};
+#ifdef CPRA_CHECKED
+void csr_check_collect_spmm(CsrCheck* r);
+void csr_check_collect_eval(CsrCheck* r);
+template <int PROBLEM> void csr_check_collect_loss(CsrCheck* r);
+template <> void csr_check_collect_loss<0>(CsrCheck* r);
+template <> void csr_check_collect_loss<1>(CsrCheck* r);
+template <> void csr_check_collect_loss<2>(CsrCheck* r);
+template <> void csr_check_collect_loss<3>(CsrCheck* r);
+template <> void csr_check_collect_loss<4>(CsrCheck* r);
+#endif
 
 }  // namespace cpra

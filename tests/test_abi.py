@@ -39,6 +39,19 @@ def test_library_exports_every_declared_symbol(L):
         assert hasattr(L, name), name
 
 
+def test_checked_library_exports_every_declared_symbol(L):
+    """The checked build (in-kernel CSR checks) is the same ABI."""
+    import ctypes
+    Lc = ctypes.CDLL(cpra.LIB_CHECKED_PATH)
+    for name in declared_functions():
+        assert hasattr(Lc, name), name
+
+
+def test_release_build_reports_no_csr_checks(L):
+    """cpra_csr_check answers -1 from the release build (no device call)."""
+    assert cpra.cpra_csr_check() == (-1, -1, -1)
+
+
 def test_config_default_and_param_counts(L):
     cfg = cpra.cpra_config_default()
     assert (cfg.problem, cfg.S, cfg.H0, cfg.H1, cfg.alpha) == (cpra.MIS, 8, 16, 16, 2)
