@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -249,6 +250,47 @@ std::string validate_config(const cpra_config* cfg) {
   return "";
 }
 
+// Rows [r0, r1) of the graph checks: column range, no self-loop, strictly
+// increasing columns, and symmetry (i appears in row j for every j in row i).
+// Returns the first failing row's message, or "".
+std::string validate_rows(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t r0,
+                          int64_t r1) {
+  for (int64_t i = r0; i < r1; ++i) {
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t j = col[e];
+      if (j < 0 || j >= N) return "column index out of range";
+      if (j == i) return "self-loop at node " + std::to_string(i);
+      if (e > rowptr[i] && col[e - 1] >= j) return "columns must be strictly increasing within a row";
+      const int32_t* b = col + rowptr[j];
+      const int32_t* en = col + rowptr[j + 1];
+      if (!std::binary_search(b, en, (int32_t)i))
+        return "graph is not symmetric: (" + std::to_string(i) + "," + std::to_string(j) + ")";
+    }
+  }
+  return "";
+}
+
+// Runs check(r0, r1) over contiguous row ranges on up to 16 host threads
+// (one for small graphs) and returns the message of the lowest failing
+// range, so the result does not depend on the thread count.
+template <typename F>
+std::string for_row_ranges(int64_t N, int64_t nnz, F check) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t T = nnz < (1 << 18) ? 1 : std::min<int64_t>(16, hw ? hw : 1);
+  T = std::max<int64_t>(1, std::min<int64_t>(T, N));
+  std::vector<std::string> msg((size_t)T);
+  std::vector<std::thread> pool;
+  auto range = [&](int64_t k) {
+    msg[(size_t)k] = check(N * k / T, N * (k + 1) / T);
+  };
+  for (int64_t k = 1; k < T; ++k) pool.emplace_back(range, k);
+  range(0);
+  for (auto& th : pool) th.join();
+  for (const auto& m : msg)
+    if (!m.empty()) return m;
+  return "";
+}
+
 std::string validate_graph(int64_t N, const int64_t* rowptr, const int32_t* col) {
   if (N < 1 || N > 0x7fffffffLL) return "N must be in [1, 2^31-1]";
   if (!rowptr) return "rowptr is NULL";
@@ -258,20 +300,9 @@ std::string validate_graph(int64_t N, const int64_t* rowptr, const int32_t* col)
   const int64_t nnz = rowptr[N];
   if (nnz >= 0x7fffffffLL) return "nnz must be < 2^31";
   if (nnz > 0 && !col) return "col is NULL";
-  for (int64_t i = 0; i < N; ++i) {
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      const int64_t j = col[e];
-      if (j < 0 || j >= N) return "column index out of range";
-      if (j == i) return "self-loop at node " + std::to_string(i);
-      if (e > rowptr[i] && col[e - 1] >= j) return "columns must be strictly increasing within a row";
-      // symmetry: i must appear in row j
-      const int32_t* b = col + rowptr[j];
-      const int32_t* en = col + rowptr[j + 1];
-      if (!std::binary_search(b, en, (int32_t)i))
-        return "graph is not symmetric: (" + std::to_string(i) + "," + std::to_string(j) + ")";
-    }
-  }
-  return "";
+  return for_row_ranges(N, nnz, [&](int64_t r0, int64_t r1) {
+    return validate_rows(N, rowptr, col, r0, r1);
+  });
 }
 
 // Split count of a weight gradient C[M x Nc] summed over the N node rows:
@@ -871,17 +902,19 @@ cpra_status check_err_flag(cpra_ctx* c) {
 std::string validate_edge_weights(int64_t N, const int64_t* rowptr, const int32_t* col,
                                   const float* w, int32_t problem) {
   if (problem != CPRA_MAXCUT) return "edge weights apply to CPRA_MAXCUT only (w must be NULL)";
-  for (int64_t i = 0; i < N; ++i)
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      if (!std::isfinite(w[e])) return "edge weights must be finite";
-      const int32_t j = col[e];
-      const int32_t* b = col + rowptr[j];
-      const int32_t* f = col + rowptr[j + 1];
-      const int32_t* it = std::lower_bound(b, f, static_cast<int32_t>(i));
-      if (it == f || *it != i || w[rowptr[j] + (it - b)] != w[e])
-        return "edge weights must be symmetric (A_ij == A_ji)";
-    }
-  return std::string();
+  return for_row_ranges(N, rowptr[N], [&](int64_t r0, int64_t r1) -> std::string {
+    for (int64_t i = r0; i < r1; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        if (!std::isfinite(w[e])) return "edge weights must be finite";
+        const int32_t j = col[e];
+        const int32_t* b = col + rowptr[j];
+        const int32_t* f = col + rowptr[j + 1];
+        const int32_t* it = std::lower_bound(b, f, static_cast<int32_t>(i));
+        if (it == f || *it != i || w[rowptr[j] + (it - b)] != w[e])
+          return "edge weights must be symmetric (A_ij == A_ji)";
+      }
+    return std::string();
+  });
 }
 
 }  // namespace

@@ -124,6 +124,43 @@ def test_invalid_graphs_rejected_on_host(L, case):
     assert st == cpra.CPRA_EINVAL, msg
 
 
+@pytest.mark.parametrize("first,second", [("range", "selfloop"), ("selfloop", "range"),
+                                          ("asym", "range")])
+def test_large_graph_reports_its_lowest_failing_row(L, first, second):
+    """Graphs with at least 2^18 entries are checked on several host threads
+    over row ranges; the message is the lowest failing row's, whatever the
+    thread count.  Each planted defect replaces the entry (r, k) of the row's
+    largest neighbour k > r, so the rows it unbalances lie above r."""
+    N, d = 100_000, 6
+    rp, col = I.random_regular_graph(N, d, seed=3)
+    col = col.copy()
+
+    def row_with_higher_neighbour(start):
+        return next(r for r in range(start, N) if col[rp[r + 1] - 1] > r)
+
+    def plant(kind, row):
+        e0, e1 = int(rp[row]), int(rp[row + 1])
+        if kind == "range":
+            col[e1 - 1] = N + 7
+            return "column index out of range"
+        if kind == "selfloop":
+            col[e1 - 1] = row
+            col[e0:e1].sort()
+            return f"self-loop at node {row}"
+        nb = set(col[e0:e1].tolist())
+        c = next(v for v in range(row + 1, N) if v not in nb)
+        col[e1 - 1] = c
+        col[e0:e1].sort()
+        return f"not symmetric: ({row},{c})"
+
+    r1 = row_with_higher_neighbour(20_000)
+    r2 = row_with_higher_neighbour(90_000)
+    want = plant(first, r1)
+    plant(second, r2)
+    st, msg = _init_status(rp, col)
+    assert st == cpra.CPRA_EINVAL and want in msg, msg
+
+
 def test_invalid_config_rejected_on_host(L):
     rp, col = I.random_regular_graph(20, 3, seed=1)
     st, _ = _init_status(rp, col, alpha=3)
