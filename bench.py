@@ -815,8 +815,8 @@ def main():
                     help="time-to-quality run: FP32 plain vs BF16 + warm start on the workload graph")
     ap.add_argument("--q-steps", type=int, default=2000)
     ap.add_argument("--q-eval", type=int, default=50)
-    ap.add_argument("--q-train", type=int, default=512)
-    ap.add_argument("--q-heldout", type=int, default=64)
+    ap.add_argument("--q-train", type=int, default=4096)
+    ap.add_argument("--q-heldout", type=int, default=256)
     ap.add_argument("--q-nmin", type=int, default=1000)
     ap.add_argument("--q-nmax", type=int, default=10000)
     ap.add_argument("--q-ref-steps", type=int, default=3000)
