@@ -1172,8 +1172,9 @@ size_t tc_smem_need(int bn, int64_t K, int stages = 2) {
 
 // Shared memory with BN columns when the weights stream with the A stages
 // (two stages at least).
-size_t tc_stream_smem_need(int bn) {
-  return 1024 + kStgTotal + 2 * (static_cast<size_t>(kStageBytes) + static_cast<size_t>(bn) * kBK * 2) +
+size_t tc_stream_smem_need(int bn, int stages = 2) {
+  return 1024 + kStgTotal +
+         static_cast<size_t>(stages) * (static_cast<size_t>(kStageBytes) + static_cast<size_t>(bn) * kBK * 2) +
          256;
 }
 
@@ -1196,11 +1197,22 @@ NPlan plan_n(int Nc, int64_t K, int64_t M = 0, int num_sms = 0, bool deep = fals
   NPlan pl;
   const int cap = Nc < 256 ? Nc : 256;
   const int want = cap < 128 ? cap : 128;
+  // A full-width tile whose resident weights leave only two A stages streams
+  // its weights with the stages instead (from L2), which keeps three: each A
+  // tile is read once, with a deeper pipeline.  At N = 10^6, K = 256, 256
+  // outputs: the split input gradient 0.204 -> 0.164 ms, the sigmoid head
+  // 0.258 -> 0.254 ms (against its two resident 128-wide tiles).
+  if (cap == 256 && tc_smem_need(cap, K, 3) > static_cast<size_t>(g_max_smem) &&
+      tc_smem_need(cap, K, 2) <= static_cast<size_t>(g_max_smem) &&
+      tc_stream_smem_need(cap, 3) <= static_cast<size_t>(g_max_smem)) {
+    pl.bn = cap;
+    pl.stream = true;
+    return pl;
+  }
   // deep: resident weights with a pipeline at least four A stages deep, on
-  // equal n tiles.  A 256-wide tile of a K = 256 product keeps only two
-  // stages; for the sigmoid head (FP32 output) two 128-wide tiles that share
-  // each A tile through L2 measured faster (0.283 -> 0.258 ms at N = 10^6),
-  // for the split input gradient (BF16 outputs) slower (0.204 -> 0.215 ms).
+  // equal n tiles (for the sigmoid head, whose FP32 output favoured two
+  // 128-wide tiles sharing each A tile through L2 over one 256-wide tile with
+  // two resident stages: 0.283 -> 0.258 ms before the streamed case above).
   if (deep)
     for (int bn = cap; bn >= want; bn -= 16)
       if (Nc % bn == 0 && tc_smem_need(bn, K, 4) <= static_cast<size_t>(g_max_smem)) {
