@@ -247,14 +247,27 @@ gemm_simt_kernel(GemmArgs g) {
   }
 }
 
+// Split-K sums in a fixed order: thread (x, y) of a 32 x 32 block adds the
+// splits z = y, y + 32, ... of output blockIdx.x * 32 + x (32 independent
+// load chains per output instead of one), then row y = 0 adds the 32 slices
+// in ascending order.
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int M,
                                      int Nc, int64_t ldp, float* out, int64_t ldo) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)M * Nc) return;
-  const int r = (int)(idx / Nc), c = (int)(idx % Nc);
+  __shared__ float sl[32][33];
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int64_t idx = (int64_t)blockIdx.x * 32 + x;
+  const bool valid = idx < (int64_t)M * Nc;
+  const int r = valid ? (int)(idx / Nc) : 0, c = valid ? (int)(idx % Nc) : 0;
   float t = 0.f;
-  for (int z = 0; z < splits; ++z) t += part[(int64_t)z * M * ldp + (int64_t)r * ldp + c];
-  out[(int64_t)r * ldo + c] = t;
+  if (valid)
+    for (int z = y; z < splits; z += 32) t += part[(int64_t)z * M * ldp + (int64_t)r * ldp + c];
+  sl[y][x] = t;
+  __syncthreads();
+  if (y == 0 && valid) {
+    float u = 0.f;
+    for (int k = 0; k < 32; ++k) u += sl[k][x];
+    out[(int64_t)r * ldo + c] = u;
+  }
 }
 
 }  // namespace
@@ -295,8 +308,8 @@ void gemm_simt_launch(const GemmArgs& g, cudaStream_t st) {
 void splitk_reduce(const float* part, int splits, int M, int Nc, int64_t ldp, float* out,
                    int64_t ldo, cudaStream_t st) {
   const int64_t n = (int64_t)M * Nc;
-  splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, splits, M, Nc, ldp,
-                                                                     out, ldo);
+  splitk_reduce_kernel<<<(unsigned)((n + 31) / 32), dim3(32, 32), 0, st>>>(part, splits, M, Nc,
+                                                                           ldp, out, ldo);
 }
 #endif
 
