@@ -726,7 +726,7 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
     // DBM: the pair counts come from the line counts below, so no edges here
     eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits,
                      dbm ? 2 : c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->counters,
-                     c->num_sms * 8, c->stream);
+                     c->num_sms, c->stream);
     if (c->w_d) {  // weighted MIS: the value of each shot in weight units
       weighted_value_launch(N, c->S, c->xbits, c->w_d, c->S_pad, c->wv_part, kWvBlocks,
                             c->wvalue, c->stream);
@@ -1886,7 +1886,7 @@ cpra_status cpra_op_round_eval(int64_t N, int32_t S, const int32_t* rowptr, cons
     return CPRA_ECUDA;
   const int sms = device_sm_count();
   loss_launch(a, sms * 4, st);  // rounding bits
-  eval_bits_launch(N, S, rowptr, col, x_bits, problem, cnt, sms * 8, st);
+  eval_bits_launch(N, S, rowptr, col, x_bits, problem, cnt, sms, st);
   eval_finalize(cnt, S, problem, lambda, out, reinterpret_cast<long long*>(pair_hamming), st);
   return cudaGetLastError() == cudaSuccess ? CPRA_OK : CPRA_ECUDA;
 }

@@ -176,9 +176,10 @@ void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
 // adds to counters obj[S] (MIS set size / MaxCut cut edges), viol[S] (MIS
 // edges inside the set) and counters[2S] = sum_i k_i (S - k_i); problem 2
 // reads no edges (set sizes and the Hamming sum only).  The counters must be
-// zeroed by the caller.
+// zeroed by the caller.  sms: the device's SM count (the grid is one wave of
+// resident blocks at most).
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
-                      int problem, unsigned long long* counters, int max_grid, cudaStream_t st);
+                      int problem, unsigned long long* counters, int sms, cudaStream_t st);
 
 // Device image of cpra_shot_eval.
 struct ShotEvalRec {

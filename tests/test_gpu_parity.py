@@ -158,9 +158,16 @@ def test_op_loss_constant_rows_have_zero_diversity_gradient():
 
 # =============================================================== round/eval
 @pytest.mark.parametrize("problem", [O.MIS, O.MAXCUT])
+# The S values reach every layout of the evaluation kernel: one 32-shot word
+# per lane for odd word counts (S = 1, 8: 8 lanes a row; 270: 16; 530: 32)
+# and two words per lane for even counts (37, 100: 2 lanes; 256: 4; 300: 8;
+# 640, 1000: 16), with rows long enough for several neighbour passes and
+# slot groups (degrees 20-40).
 @pytest.mark.parametrize("S,N,gk", [(8, 1000, ("rrg", 3)), (37, 2001, ("er", 6)),
                                      (100, 1500, ("rrg", 20)), (256, 999, ("er", 5)),
-                                     (1000, 200, ("er", 3)), (1, 50, ("rrg", 4))])
+                                     (1000, 200, ("er", 3)), (1, 50, ("rrg", 4)),
+                                     (300, 700, ("rrg", 9)), (270, 500, ("er", 12)),
+                                     (530, 300, ("er", 40)), (640, 400, ("er", 30))])
 def test_op_round_eval_bit_exact(problem, S, N, gk):
     rp, col = graph_of(gk, N, seed=7 * S + N)
     g = O.Graph(rp, col)
