@@ -358,7 +358,7 @@ size_t carve(cpra_ctx* c, void* base) {
   c->pstride = loss_pstride(c->S);
   c->loss_part = cv.take<float>((size_t)kLossMaxGrid * c->pstride);
   c->terms = cv.take<float>(4 * (size_t)c->S + 1);
-  c->counters = cv.take<unsigned long long>(2 * (size_t)c->S + 1);
+  c->counters = cv.take<unsigned long long>(2 * (size_t)c->S + 2);  // + the last-block ticket
   c->eval_rec = cv.take<cpra_shot_eval>(c->S);
   c->ham_d = cv.take<long long>(1);
   c->colsum_part = cv.take<float>((size_t)kLossMaxGrid * c->H1);
@@ -721,12 +721,8 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
   }
   {  // exact integer evaluation of the rounded shots
     Region r(c, K_EVAL);
-    cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 1) * sizeof(unsigned long long),
-                    c->stream);
-    // DBM: the pair counts come from the line counts below, so no edges here
-    eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits,
-                     dbm ? 2 : c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->counters,
-                     c->num_sms, c->stream);
+    // shot values first (they read only the bits): the evaluation's last
+    // block puts them into the records
     if (c->w_d) {  // weighted MIS: the value of each shot in weight units
       weighted_value_launch(N, c->S, c->xbits, c->w_d, c->S_pad, c->wv_part, kWvBlocks,
                             c->wvalue, c->stream);
@@ -738,14 +734,26 @@ cpra_status run_forward_and_loss(cpra_ctx* c, float gamma, bool do_loss,
       c->launches += 2;
     }
     if (dbm) {  // matchings: line counts, constraints and rewards (the set size and
-                // pair-Hamming counters above are problem-independent)
+                // pair-Hamming counters of the evaluation are problem-independent;
+                // the pair counts come from the line counts, so no edges here)
+      cudaMemsetAsync(c->counters, 0, (2 * (size_t)c->S + 2) * sizeof(unsigned long long),
+                      c->stream);
+      eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits, 2, c->counters, c->num_sms,
+                       c->stream);
       dbm_eval_launch(c->dbm, c->S, c->xbits, c->counters, c->eval_rec, c->ham_d, c->stream);
       c->launches += 3;
     } else {
-      eval_finalize(c->counters, c->S, c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->lambda_d,
-                    c->eval_rec, c->ham_d, c->stream,
-                    c->w_d ? c->wvalue : c->ew_d ? c->cutw : nullptr);
-      c->launches += 2;
+      // the counters are zero here (set at creation, reset by the last block
+      // of every evaluation), and the launch writes the records itself
+      EvalFinalize fin;
+      fin.lambda = c->lambda_d;
+      fin.wvalue = c->w_d ? c->wvalue : c->ew_d ? c->cutw : nullptr;
+      fin.records = c->eval_rec;
+      fin.ham = c->ham_d;
+      eval_bits_launch(N, c->S, c->rowptr, c->col, c->xbits,
+                       c->cfg.problem == CPRA_MAXCUT ? 1 : 0, c->counters, c->num_sms, c->stream,
+                       &fin);
+      c->launches += 1;
     }
   }
   c->have_eval = true;
@@ -1090,6 +1098,7 @@ cpra_status cpra_init_graph(cpra_ctx** out, int64_t N, const int64_t* rowptr,
   cudaMemsetAsync(c->err_flag, 0, sizeof(int) * 4, st);
   reset_early_stop(c);
   cudaMemsetAsync(c->terms, 0, sizeof(float) * (4 * c->S + 1), st);
+  cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * (2 * (size_t)c->S + 2), st);
   if (c->w_d) fill_rows_launch(N, c->S, c->S_pad, 1.f, c->w_d, st);  // weights 1 until set
   // parameters: U(+-1/sqrt(fan_in)) for weights and biases, N(0,1) embeddings
   const Layout L = layout_of(c->H0, c->H1, c->S);

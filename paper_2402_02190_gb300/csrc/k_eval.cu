@@ -308,7 +308,7 @@ template <int L, int V, int PROBLEM>
 __global__ void __launch_bounds__(256, 3)
 eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
                  const int* __restrict__ col, const uint32_t* __restrict__ bits,
-                 unsigned long long* counters) {
+                 unsigned long long* counters, const EvalFinalize fin) {
   constexpr bool kEdges = PROBLEM != 2;  // DBM: set sizes and the Hamming sum only
   constexpr bool kSizes = PROBLEM != 1;  // MaxCut: cut edges only
   constexpr int CPL = L >= 8 ? 1 : 8 / L;
@@ -410,11 +410,47 @@ eval_bits_kernel(int64_t N, int S, int W, const int* __restrict__ rowptr,
     if (scnt[Wpad + s]) atomicAdd(&counters[S + s], (unsigned long long)scnt[Wpad + s]);
   }
   if (threadIdx.x == 0 && ham_s) atomicAdd(&counters[2 * S], ham_s);
+  if constexpr (PROBLEM != 2) {
+    if (fin.records) {
+      // the block's additions are visible device-wide before its ticket;
+      // the last block then sees every block's additions
+      __shared__ bool last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned long long t =
+            atomicAdd(&counters[2 * S + 1], 1ull);
+        last = t == (unsigned long long)gridDim.x - 1ull;
+      }
+      __syncthreads();
+      if (last) {
+        __threadfence();
+        volatile unsigned long long* vc = counters;
+        ShotEvalRec* rec = static_cast<ShotEvalRec*>(fin.records);
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
+          const long long obj = (long long)vc[s];
+          const long long viol = (long long)vc[S + s];
+          const double value = fin.wvalue ? fin.wvalue[s] : (double)obj;
+          rec[s].objective = obj;
+          rec[s].violations = PROBLEM == 0 ? viol : 0;
+          rec[s].qubo = PROBLEM == 0 ? -value + (double)fin.lambda[s] * (double)viol : -value;
+          rec[s].value = value;
+          vc[s] = 0ull;
+          vc[S + s] = 0ull;
+        }
+        if (threadIdx.x == 0) {
+          if (fin.ham) *fin.ham = (long long)vc[2 * S];
+          vc[2 * S] = 0ull;
+          vc[2 * S + 1] = 0ull;
+        }
+      }
+    }
+  }
 }
 
 template <int L, int V, int PROBLEM>
 void launch_lp(int64_t N, int S, int W, const int* rowptr, const int* col, const uint32_t* bits,
-               unsigned long long* counters, int sms, cudaStream_t st) {
+               unsigned long long* counters, int sms, cudaStream_t st, const EvalFinalize& fin) {
   // one wave of resident blocks: the rows are spread evenly over the
   // segments, so a second, partial wave would only add a tail
   static const int per_sm = [] {
@@ -435,18 +471,20 @@ void launch_lp(int64_t N, int S, int W, const int* rowptr, const int* col, const
   const int64_t want = blocks(threads);
   const int64_t wave = (int64_t)per_sm * sms;
   const int grid = (int)(want < wave ? (want > 0 ? want : 1) : wave);
-  eval_bits_kernel<L, V, PROBLEM><<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters);
+  eval_bits_kernel<L, V, PROBLEM>
+      <<<grid, threads, 0, st>>>(N, S, W, rowptr, col, bits, counters, fin);
 }
 
 template <int L, int V>
 void launch_l(int64_t N, int S, int W, const int* rowptr, const int* col, const uint32_t* bits,
-              int problem, unsigned long long* counters, int sms, cudaStream_t st) {
+              int problem, unsigned long long* counters, int sms, cudaStream_t st,
+              const EvalFinalize& fin) {
   if (problem == 0)
-    launch_lp<L, V, 0>(N, S, W, rowptr, col, bits, counters, sms, st);
+    launch_lp<L, V, 0>(N, S, W, rowptr, col, bits, counters, sms, st, fin);
   else if (problem == 1)
-    launch_lp<L, V, 1>(N, S, W, rowptr, col, bits, counters, sms, st);
+    launch_lp<L, V, 1>(N, S, W, rowptr, col, bits, counters, sms, st, fin);
   else
-    launch_lp<L, V, 2>(N, S, W, rowptr, col, bits, counters, sms, st);
+    launch_lp<L, V, 2>(N, S, W, rowptr, col, bits, counters, sms, st, fin);
 }
 
 // Weighted MIS value per shot: block b sums w_is over its row range for the
@@ -523,17 +561,20 @@ void weighted_value_launch(int64_t N, int S, const uint32_t* bits, const float* 
 }
 
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
-                      int problem, unsigned long long* counters, int sms, cudaStream_t st) {
+                      int problem, unsigned long long* counters, int sms, cudaStream_t st,
+                      const EvalFinalize* fin) {
   const int W = (S + 31) / 32;
+  EvalFinalize f;
+  if (fin && problem != 2) f = *fin;
   if (W % 2 == 0) {  // two words per lane
-    if (W <= 4) launch_l<2, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
-    else if (W <= 8) launch_l<4, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
-    else if (W <= 16) launch_l<8, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
-    else launch_l<16, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
+    if (W <= 4) launch_l<2, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
+    else if (W <= 8) launch_l<4, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
+    else if (W <= 16) launch_l<8, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
+    else launch_l<16, 2>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
   } else {
-    if (W <= 8) launch_l<8, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
-    else if (W <= 16) launch_l<16, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
-    else launch_l<32, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st);
+    if (W <= 8) launch_l<8, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
+    else if (W <= 16) launch_l<16, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
+    else launch_l<32, 1>(N, S, W, rowptr, col, bits, problem, counters, sms, st, f);
   }
 }
 

@@ -178,8 +178,21 @@ void colsum_finalize(const float* part, int nblocks, int64_t pstride, int ncols,
 // reads no edges (set sizes and the Hamming sum only).  The counters must be
 // zeroed by the caller.  sms: the device's SM count (the grid is one wave of
 // resident blocks at most).
+//
+// With fin (problems 0 and 1 only) the launch also writes the per-shot
+// records: the last block to finish (a ticket in counters[2S+1]) reads the
+// counters, writes the records as eval_finalize does, and sets counters
+// [0, 2S+1] back to zero, so the next launch needs no reset.  The counters
+// array then holds 2S+2 words, zero before the first such launch.
+struct EvalFinalize {
+  const float* lambda = nullptr;   // MIS penalty weights [S]
+  const double* wvalue = nullptr;  // shot values (weighted MIS / MaxCut), or null
+  void* records = nullptr;         // ShotEvalRec [S]
+  long long* ham = nullptr;        // pair-Hamming total, or null
+};
 void eval_bits_launch(int64_t N, int S, const int* rowptr, const int* col, const uint32_t* bits,
-                      int problem, unsigned long long* counters, int sms, cudaStream_t st);
+                      int problem, unsigned long long* counters, int sms, cudaStream_t st,
+                      const EvalFinalize* fin = nullptr);
 
 // Device image of cpra_shot_eval.
 struct ShotEvalRec {
