@@ -648,31 +648,44 @@ def run_quality_compact(args):
     """A compact form of the time-to-quality race for the default line: MIS on
     a seeded 5-regular graph of 2*10^5 nodes (S = 256, H = 128, the default
     workload's shots and widths), 2000-step schedules, evaluation every 50
-    steps; the warm-start network trained on 96 small graphs (N 1,000-5,000,
-    1000-step targets).  Arms as in --quality: FP32 (split-TF32 engine), BF16
-    plain, BF16 plain with the warm arm's schedule, BF16 + warm start."""
+    steps; the warm-start network trained on 512 small graphs (N 1,000-5,000,
+    1000-step targets) whose targets come from multi-instance solves: the
+    graphs are packed into disjoint unions of up to 2*10^5 nodes and each
+    union is solved by one CPRA run.  Arms as in --quality: FP32 (split-TF32
+    engine), BF16 plain, BF16 plain with the warm arm's schedule, BF16 + warm
+    start.  The first 8 training graphs are also solved one by one, to report
+    how the union-solved targets compare."""
     import torch
     from paper_2402_02190_gb300 import cpra
     from paper_2402_02190_gb300 import warm as WM
     S, H, steps, ev = 256, 128, 2000, 50
-    n_train, target_steps = 96, 1000
+    n_train, target_steps, union_nodes, n_check = 512, 1000, 200_000, 8
     lam = I.lambda_geomspace(0.5, 10.0, S)
     g0 = args.q_warm_gamma0
+    graphs = WM.training_graphs(n_train, seed=78, n_min=1000, n_max=5000)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    graphs = WM.training_graphs(n_train, seed=78, n_min=1000, n_max=5000)
-    dataset = []
-    for k, (rp, col, d) in enumerate(graphs):
-        bits, _ = WM.cpra_targets(rp, col, S, lam, target_steps, cpra.BF16, H=64, seed=k + 1)
-        dataset.append((rp, col, bits, 2000 + k))
+    tbits = WM.cpra_targets_union([(g[0], g[1]) for g in graphs], S, lam, target_steps,
+                                  cpra.BF16, H=64, seed=1, max_nodes=union_nodes)
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    dataset = [(g[0], g[1], b, 2000 + k) for k, (g, b) in enumerate(zip(graphs, tbits))]
     net = cpra.WarmStartNet(max(len(g[0]) - 1 for g in graphs) * 8,
                             max(int(g[0][-1]) for g in graphs) * 8, F=16, H=64, S=S,
                             precision=cpra.BF16, lr=3e-3)
+    t0 = time.perf_counter()
     WM.train_network(net, dataset, 40, 8)
     theta = net.params(0)
     net.close()
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    t_fit = time.perf_counter() - t0
+    # union-solved targets against separate solves of the same graphs
+    check = []
+    for k in range(n_check):
+        rp_k, col_k, _ = graphs[k]
+        sep, _ = WM.cpra_targets(rp_k, col_k, S, lam, target_steps, cpra.BF16, H=64, seed=1)
+        check.append((WM.mis_best_from_bits(rp_k, col_k, tbits[k], S),
+                      WM.mis_best_from_bits(rp_k, col_k, sep, S)))
     rp, col = I.random_regular_graph(2 * 10**5, 5, seed=55)
     fp32 = WM.run_trace(rp, col, S, lam, steps, ev, cpra.FP32, H=H, seed=1)
     target = 0.99 * fp32[-1][2]
@@ -694,7 +707,12 @@ def run_quality_compact(args):
     return {"metric": "wall seconds to within 1% of the FP32 form's best MIS", "unit": "s",
             "graph": "rrg degree 5, N=200000, seed 55", "S": S, "H": H, "steps": steps,
             "eval_every": ev, "warm_gamma0": g0,
-            "warm_training": {"graphs": n_train, "target_steps": target_steps, "seconds": t_train},
+            "warm_training": {"graphs": n_train, "target_steps": target_steps,
+                              "targets": "multi-instance: disjoint unions of up to %d nodes, "
+                                         "one CPRA run each" % union_nodes,
+                              "target_seconds": t_targets, "fit_seconds": t_fit,
+                              "seconds": t_targets + t_fit,
+                              "union_vs_separate_best_mis": [list(c) for c in check]},
             "fp32": arm(fp32), "bf16_plain": arm(plain), "bf16_plain_matched_schedule": arm(matched),
             "bf16_warm": arm(warm),
             "how": "compact form of bench.py --quality; wall clock from context creation "

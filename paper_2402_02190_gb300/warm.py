@@ -54,6 +54,54 @@ def cpra_targets(rp, col, S: int, lam, steps: int, precision: int = cpra.BF16, H
     return bits, rec
 
 
+def cpra_targets_union(graphs, S: int, lam, steps: int, precision: int = cpra.BF16, H: int = 64,
+                       seed: int = 1, max_nodes: int = 200_000, problem: int = cpra.MIS):
+    """Plain CPRA on many graphs at once (the paper's multi-instance form):
+    the graphs, in order, are packed into disjoint unions of at most
+    `max_nodes` nodes, one CPRA run of `steps` steps solves each union (one
+    network, one embedding row per node; union u uses seed + u), and the
+    union's rounded bits are split back per graph.  Returns
+    [bits (uint32 [N_k, ceil(S/32)])]."""
+    out, group, nodes, unions = [], [], 0, [0]
+
+    def flush():
+        if not group:
+            return
+        rp, col = disjoint_union([(g[0], g[1]) for g in group])
+        bits, _ = cpra_targets(rp, col, S, lam, steps, precision, H=H, seed=seed + unions[0],
+                               problem=problem)
+        unions[0] += 1
+        off = 0
+        for g in group:
+            n = len(g[0]) - 1
+            out.append(np.ascontiguousarray(bits[off:off + n]))
+            off += n
+
+    for g in graphs:
+        n = len(g[0]) - 1
+        if group and nodes + n > max_nodes:
+            flush()
+            group, nodes = [], 0
+        group.append(g)
+        nodes += n
+    flush()
+    return out
+
+
+def mis_best_from_bits(rp, col, bits, S: int) -> int:
+    """Largest MIS size among the shots of packed solution bits that have no
+    violated edge (host arithmetic, for reports on small graphs)."""
+    bits = np.asarray(bits).view(np.uint32)
+    x = np.zeros((bits.shape[0], S), dtype=bool)
+    for s in range(S):
+        x[:, s] = (bits[:, s // 32] >> np.uint32(s % 32)) & np.uint32(1)
+    ei, ej = I.csr_to_edges(np.asarray(rp), np.asarray(col))
+    viol = (x[ei] & x[ej]).sum(axis=0)
+    size = x.sum(axis=0)
+    ok = viol == 0
+    return int(size[ok].max()) if ok.any() else -1
+
+
 def train_network(net, dataset, epochs: int, batch_graphs: int, seed: int = 0, device="cuda"):
     """Fits the network on disjoint unions of `batch_graphs` training graphs.
     dataset: [(rowptr, col, bits, graph_seed)].  Returns the per-epoch mean loss."""

@@ -47,3 +47,42 @@ def test_time_to_reach_and_best_feasible():
     rec["violations"] = [0, 2, 0]
     assert WM.best_feasible(rec) == 7
     assert WM.best_feasible(rec, problem=1) == 9
+
+
+def test_union_targets_pack_in_order_and_split_back(monkeypatch):
+    """Multi-instance target solves: graphs are packed in order into unions of
+    at most max_nodes nodes, each union is solved once, and each graph gets
+    back exactly its own rows of the union's bits."""
+    graphs = [(r, c) for r, c, _ in WM.training_graphs(6, seed=3, n_min=20, n_max=40)]
+    sizes = [len(r) - 1 for r, _ in graphs]
+    solved = []
+
+    def fake_solve(rp, col, S, lam, steps, precision, H=64, seed=1, problem=0):
+        # row i of the union carries its union row index, so a graph's slice
+        # tells where it was cut from
+        solved.append((len(rp) - 1, seed))
+        assert np.all(np.diff(rp) >= 0)
+        N = len(rp) - 1
+        return np.arange(N, dtype=np.uint32)[:, None].repeat((S + 31) // 32, 1), None
+
+    monkeypatch.setattr(WM, "cpra_targets", fake_solve)
+    out = WM.cpra_targets_union(graphs, 64, None, 10, max_nodes=70, seed=5)
+    # greedy packing in order, never above the budget
+    unions, cur = [], 0
+    for n in sizes:
+        if cur and cur + n > 70:
+            unions.append(cur)
+            cur = 0
+        cur += n
+    unions.append(cur)
+    assert [u for u, _ in solved] == unions
+    assert [s for _, s in solved] == [5 + k for k in range(len(unions))]
+    assert [o.shape for o in out] == [(n, 2) for n in sizes]
+    k = 0
+    for u in unions:
+        off = 0
+        while off < u:
+            assert np.array_equal(out[k][:, 0], np.arange(off, off + sizes[k]))
+            off += sizes[k]
+            k += 1
+    assert k == len(graphs)
