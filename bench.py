@@ -505,7 +505,8 @@ def run_quality(args):
            "config": {"workload": args.workload, "steps": q, "eval_every": args.q_eval,
                       "warm_gamma0": g0, "warm_graphs": args.q_train,
                       "warm_heldout": args.q_heldout, "graph_nodes": [args.q_nmin, args.q_nmax],
-                      "target_steps": args.q_target_steps, "heldout_ref_steps": args.q_ref_steps}}
+                      "target_steps": args.q_target_steps, "heldout_ref_steps": args.q_ref_steps,
+                      "target_union_nodes": args.q_union_nodes}}
     # 1. targets from plain CPRA (BF16, full schedule) on seeded training graphs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -515,9 +516,15 @@ def run_quality(args):
     train, held = graphs[:args.q_train], graphs[args.q_train:]
     t0 = time.perf_counter()
     dataset = []
-    for k, (rp, col, d) in enumerate(train):
-        bits, _ = WM.cpra_targets(rp, col, S, lam, args.q_target_steps, cpra.BF16, H=64, seed=k + 1)
-        dataset.append((rp, col, bits, 1000 + k))
+    if args.q_union_nodes > 0:  # multi-instance solves of disjoint unions
+        tbits = WM.cpra_targets_union([(g[0], g[1]) for g in train], S, lam, args.q_target_steps,
+                                      cpra.BF16, H=64, seed=1, max_nodes=args.q_union_nodes)
+        dataset = [(g[0], g[1], b, 1000 + k) for k, (g, b) in enumerate(zip(train, tbits))]
+    else:
+        for k, (rp, col, d) in enumerate(train):
+            bits, _ = WM.cpra_targets(rp, col, S, lam, args.q_target_steps, cpra.BF16, H=64,
+                                      seed=k + 1)
+            dataset.append((rp, col, bits, 1000 + k))
     torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     # 2. fit the warm-start network
@@ -839,6 +846,9 @@ def main():
     ap.add_argument("--q-nmax", type=int, default=10000)
     ap.add_argument("--q-ref-steps", type=int, default=3000)
     ap.add_argument("--q-target-steps", type=int, default=1000)
+    ap.add_argument("--q-union-nodes", type=int, default=0,
+                    help="solve the training targets as disjoint unions of up to this many "
+                         "nodes (multi-instance CPRA); 0: one solve per graph")
     ap.add_argument("--q-epochs", type=int, default=40)
     ap.add_argument("--q-batch", type=int, default=8)
     ap.add_argument("--q-warm-gamma0", type=float, default=-0.5)
