@@ -28,7 +28,10 @@ enum SpmmKind {
 
 // LMODE: 0 CSR gathers, 1 line sums, 2 either, chosen at run time
 template <typename TX, typename TY, int LPR, int CPL, int KIND, int LMODE>
-__global__ void __launch_bounds__(256, CPL > 1 ? 1 : (KIND == KIND_MEAN || KIND == KIND_ADD ? 5 : 4))
+__global__ void __launch_bounds__(256, CPL > 1 ? 1
+                            : KIND == KIND_MEAN ? (LMODE == 1 ? 6 : 5)
+                            : KIND == KIND_ADD  ? 5
+                                                : 4)
 spmm_rows_kernel(SpmmArgs a) {
   if (a.nsl > 1) {  // column slice blockIdx.y of nsl: shift every operand
     const int chunks = a.h_full / 16, k = blockIdx.y;
@@ -58,15 +61,20 @@ spmm_rows_kernel(SpmmArgs a) {
   constexpr bool MASK_BITS = KIND == KIND_ADD_MASKBITS_COLSUM;
   constexpr bool COLSUM = KIND == KIND_ADD_MASK_COLSUM || KIND == KIND_ADD_MASKBITS_COLSUM;
   constexpr bool ADAM = KIND == KIND_ADD_ADAM;
-  // Neighbour rows per gather pass.  The mean aggregation, the masked adjoint
-  // (mask as bits) and the embedding-gradient aggregation issue one predicated
-  // batch of PB rows, so a row of degree <= PB costs one memory round trip
-  // (degree 5, H = 128, N = 10^6: mean 0.261 -> 0.253 ms at five blocks per
-  // SM instead of six, masked adjoint 0.354 -> 0.329 ms, embedding gradient
-  // with Adam 0.780 -> 0.776 ms); the other kinds gather full batches of four
-  // and then the remainder one row at a time.
-  constexpr int PB =
-      (KIND == KIND_MEAN || KIND == KIND_ADD_MASKBITS_COLSUM || KIND == KIND_ADD_ADAM) ? 5 : 0;
+  // Neighbour rows per gather pass.  With one 16-byte chunk per lane (CPL =
+  // 1) the mean aggregation, the masked adjoint (mask as bits) and the
+  // embedding-gradient aggregation issue one predicated batch of PB rows, so
+  // a row of degree <= PB costs one memory round trip (degree 5, H = 128,
+  // N = 10^6: mean 0.261 -> 0.253 ms at five blocks per SM instead of six,
+  // masked adjoint 0.354 -> 0.329 ms, embedding gradient with Adam 0.780 ->
+  // 0.776 ms).  The other kinds, and wide rows (CPL > 1, already CPL loads
+  // per neighbour and lane), gather full batches of four and then the
+  // remainder one row at a time.  The line-sum instance gathers nothing.
+  constexpr int PB = (CPL == 1 && LMODE != 1 &&
+                      (KIND == KIND_MEAN || KIND == KIND_ADD_MASKBITS_COLSUM ||
+                       KIND == KIND_ADD_ADAM))
+                         ? 5
+                         : 0;
   constexpr int VEC = V16<TX>::n;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LPR - 1);
