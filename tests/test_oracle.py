@@ -342,6 +342,40 @@ def test_relu_decision_in_bf16_only_moves_near_zero_signs():
     assert np.array_equal(a["relu_on"], a["Z1"] > 0)
 
 
+def test_relu_decision_in_bf16_flips_only_within_the_rounding_bound():
+    """The BF16 reading of the ReLU sign (operands rounded to bfloat16, unit
+    roundoff u = 2^-8) may only disagree with the FP64 sign where |Z1| is
+    within the worst-case error that rounding X0, the neighbour mean and the
+    layer-1 weights can put into Z1:
+      |dX0| |B1|^T + |bf(X0)| |dB1|^T + |dM1| |W1|^T + |bf(M1)| |dW1|^T,
+    with |dX0| <= u|X0|, |dB1| <= u|B1|, |dW1| <= u|W1|, and
+    |dM1| <= u mean|X0| + (u + 2^-23) |mean bf(X0)| (the mean of rounded
+    rows, rounded once more through float32).  A decision taken on the wrong
+    operand, transposed weights or a missing term flips signs outside it."""
+    N, H0, H1, S = 600, 32, 32, 8
+    rp, col = I.random_regular_graph(N, 5, 7)
+    g = O.Graph(rp, col)
+    theta, X0 = I.seeded_params(N, H0, H1, S, seed=11)
+    theta = theta.astype(np.float64)
+    X0 = X0.astype(np.float64)
+    a = O.forward(g, theta, X0, H0, H1, S)
+    b = O.forward(g, theta, X0, H0, H1, S, relu_decision="bf16")
+    p = O.unpack(theta, H0, H1, S)
+    u = 2.0 ** -8
+    aB, aW = np.abs(p["B1"]), np.abs(p["W1"])
+    xb = np.abs(O.bf16_round(X0))
+    mx = O.mean_aggregate(g, O.bf16_round(X0))
+    bound = (u * np.abs(X0) @ aB.T + xb @ (u * aB).T
+             + (u * O.mean_aggregate(g, np.abs(X0)) + (u + 2.0 ** -23) * np.abs(mx)) @ aW.T
+             + np.abs(O.bf16_round(mx)) @ (u * aW).T)
+    bound = bound * (1 + 1e-9) + 1e-300
+    flipped = a["relu_on"] != b["relu_on"]
+    assert flipped.sum() > 0                      # the case exercises the reading
+    assert np.all(np.abs(a["Z1"][flipped]) <= bound[flipped])
+    # and it is a rounding-level reading: few entries are that close to 0
+    assert (np.abs(a["Z1"]) <= bound).mean() < 0.05
+
+
 def test_adam_first_step_closed_form():
     g = np.array([3.0, -2e-3, 0.0, 1e-12])
     th, m, v = O.adam(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, lr=0.1)
