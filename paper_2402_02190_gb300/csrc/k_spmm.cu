@@ -198,42 +198,42 @@ spmm_rows_kernel(SpmmArgs a) {
               }
         }
       } else {
-      for (; k + 4 <= cnt; k += 4) {
-        uint4 raw[4][CPL];
+        for (; k + 4 <= cnt; k += 4) {
+          uint4 raw[4][CPL];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = __shfl_sync(smask, jc, k + u, LPR);
+          for (int u = 0; u < 4; ++u) {
+            const int j = __shfl_sync(smask, jc, k + u, LPR);
+            const TX* row = X + (int64_t)j * a.ldx;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              const int ch = c * LPR + sub;
+              raw[u][c] = (ch < nchunks) ? ldg_nc16(row + ch * VEC) : make_uint4(0, 0, 0, 0);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              float f[VEC];
+              widen(raw[u][c], f, (const TX*)nullptr);
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) acc[c][v] += f[v];
+            }
+        }
+        for (; k < cnt; ++k) {
+          const int j = __shfl_sync(smask, jc, k, LPR);
           const TX* row = X + (int64_t)j * a.ldx;
 #pragma unroll
           for (int c = 0; c < CPL; ++c) {
             const int ch = c * LPR + sub;
-            raw[u][c] = (ch < nchunks) ? ldg_nc16(row + ch * VEC) : make_uint4(0, 0, 0, 0);
+            if (ch < nchunks) {
+              float f[VEC];
+              widen(ldg_nc16(row + ch * VEC), f, (const TX*)nullptr);
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) acc[c][v] += f[v];
+            }
           }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            float f[VEC];
-            widen(raw[u][c], f, (const TX*)nullptr);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] += f[v];
-          }
-      }
-      for (; k < cnt; ++k) {
-        const int j = __shfl_sync(smask, jc, k, LPR);
-        const TX* row = X + (int64_t)j * a.ldx;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int ch = c * LPR + sub;
-          if (ch < nchunks) {
-            float f[VEC];
-            widen(ldg_nc16(row + ch * VEC), f, (const TX*)nullptr);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] += f[v];
-          }
-        }
-      }
       }
     }
 
