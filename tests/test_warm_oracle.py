@@ -80,3 +80,31 @@ def test_bf16_relu_decision_only_moves_the_mask():
     d1 = a["on1"] != b["on1"]
     assert np.all(np.abs(a["Z1"][d1]) < 0.05)
     assert np.array_equal(a["Z1"], b["Z1"])
+
+
+def test_bf16_layer1_decision_flips_only_within_the_rounding_bound():
+    """Layer 1 of the warm network under the BF16 reading: its ReLU sign may
+    only differ from the FP64 sign where |Z1| is within the worst-case error
+    that bfloat16 rounding (through float32: u = 2^-8 + 2^-22 relative) of X,
+    of the neighbour mean of the rounded rows and of W1 can put into Z1;
+    a decision taken on a wrong operand or without the bias would flip signs
+    outside that bound."""
+    F, H, S, N = 16, 32, 8, 600
+    rp, col = I.random_regular_graph(N, 5, 3)
+    g = O.Graph(rp, col)
+    rng = np.random.default_rng(4)
+    theta = rng.normal(size=WO.param_count(F, H, S)) * 0.3
+    X = rng.normal(size=(N, F))
+    a = WO.forward(g, theta, X, F, H, S)
+    b = WO.forward(g, theta, X, F, H, S, relu_decision="bf16")
+    W1 = np.abs(WO.unpack(theta, F, H, S)["W1"])          # H x 2F, [self | neighbour]
+    u = 2.0 ** -8 + 2.0 ** -22
+    mb = O.mean_aggregate(g, O.bf16_round(X))
+    dA = np.concatenate([u * np.abs(X),
+                         u * O.mean_aggregate(g, np.abs(X)) + u * np.abs(mb)], axis=1)
+    E0 = np.concatenate([np.abs(O.bf16_round(X)), np.abs(O.bf16_round(mb))], axis=1)
+    bound = (dA @ W1.T + E0 @ (u * W1).T) * (1 + 1e-9) + 1e-300
+    flipped = a["on1"] != b["on1"]
+    assert flipped.sum() > 0
+    assert np.all(np.abs(a["Z1"][flipped]) <= bound[flipped])
+    assert (np.abs(a["Z1"]) <= bound).mean() < 0.05
